@@ -1,0 +1,158 @@
+"""Hand-built cell-conversion cases for the oracle (no GPU).
+
+Expected classes are written out by hand from the rules: Sec. 2.2 (interface
+cells fill at phi >= 1 + eps and empty at phi <= -eps; gas neighbours of a
+filled cell and liquid neighbours of an emptied cell become interface), and
+Sec. 2.4 (a cell uncovered by a body becomes gas when its non-obstacle
+neighbourhood B(x) holds no liquid, liquid when it holds no gas, interface when
+it holds both).
+"""
+import numpy as np
+
+import oracle
+from paper_1201_0351_gb300 import inputs as I
+
+L_, I_, G_, O_ = I.LIQUID, I.INTERFACE, I.GAS, oracle.OBSTACLE
+
+NEIGH = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+         if abs(dx) + abs(dy) + abs(dz) in (1, 2)]
+
+
+def _layered(n, z_surface, box=None, g=0.0):
+    """liquid below z_surface, interface layer (phi 0.5) at z_surface, gas above"""
+    flags = np.full((n, n, n), G_, np.uint8)
+    fill = np.zeros((n, n, n))
+    flags[:z_surface] = L_
+    fill[:z_surface] = 1.0
+    flags[z_surface] = I_
+    fill[z_surface] = 0.5
+    rho = np.ones((n, n, n))
+    return flags, fill, rho
+
+
+def _sim(n, flags, fill, rho, boxes=()):
+    sc = I.Scenario("conv", n, n, n, 0, 0.7, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2,
+                    flags.reshape(-1).copy(), fill.reshape(-1).copy(), rho.reshape(-1).copy(), list(boxes), 0)
+    return oracle.OracleSim(sc)
+
+
+def _ledger_ok(s):
+    L = s.ledger()
+    return abs(L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"])) <= 1e-12 * L["M0"]
+
+
+def test_filled_cell_converts_and_gas_neighbours_join_interface():
+    n = 8
+    flags, fill, rho = _layered(n, 3)
+    fill[3, 3, 3] = 1.6
+    s = _sim(n, flags, fill, rho)
+    s.step(1)
+    got = s.fields()["flags"].reshape(n, n, n)
+    exp = flags.copy()
+    exp[3, 3, 3] = L_
+    for dx, dy, dz in NEIGH:
+        if dz == 1:
+            exp[4 + 0 * dz, 3 + dy, 3 + dx] = I_
+    assert np.array_equal(got, exp)
+    c = s.counts()
+    assert (c["filled"], c["emptied"], c["new_from_gas"], c["new_from_liquid"]) == (1, 0, 5, 0)
+    # the five new interface cells each receive the same 1/13 share of the excess
+    m = s.fields()["mass"].reshape(n, n, n)
+    new = [m[4, 3 + dy, 3 + dx] for dx, dy, dz in NEIGH if dz == 1]
+    assert np.ptp(new) == 0.0 and new[0] > 0.03
+    assert _ledger_ok(s)
+
+
+def test_emptied_cell_converts_and_liquid_neighbours_join_interface():
+    n = 8
+    flags, fill, rho = _layered(n, 3)
+    fill[3, 3, 3] = -0.5
+    s = _sim(n, flags, fill, rho)
+    s.step(1)
+    f = s.fields()
+    got = f["flags"].reshape(n, n, n)
+    exp = flags.copy()
+    exp[3, 3, 3] = G_
+    for dx, dy, dz in NEIGH:
+        if dz == -1:
+            exp[2, 3 + dy, 3 + dx] = I_
+    assert np.array_equal(got, exp)
+    fl = f["fill"].reshape(n, n, n)
+    for dx, dy, dz in NEIGH:
+        if dz == -1:
+            assert 0.9 < fl[2, 3 + dy, 3 + dx] < 1.0  # phi = 1 plus a share of the negative excess
+    assert _ledger_ok(s)
+
+
+def test_emptied_next_to_filled_is_kept():
+    n = 8
+    flags, fill, rho = _layered(n, 3)
+    fill[3, 3, 3] = 1.6
+    fill[3, 3, 4] = -0.5
+    s = _sim(n, flags, fill, rho)
+    s.step(1)
+    got = s.fields()["flags"].reshape(n, n, n)
+    exp = flags.copy()
+    exp[3, 3, 3] = L_
+    for dx, dy, dz in NEIGH:
+        if dz == 1:
+            exp[4, 3 + dy, 3 + dx] = I_
+    assert np.array_equal(got, exp)  # (4,3,3) stayed interface, no liquid became interface
+    c = s.counts()
+    assert (c["filled"], c["emptied"], c["new_from_liquid"]) == (1, 0, 0)
+    assert _ledger_ok(s)
+
+
+def _moving_box_scene(n, z_surface=None):
+    if z_surface is None:
+        flags = np.full((n, n, n), L_, np.uint8)
+        fill = np.ones((n, n, n))
+        rho = np.ones((n, n, n))
+    else:
+        flags, fill, rho = _layered(n, z_surface)
+    return flags, fill, rho
+
+
+def test_box_moving_through_liquid_uncovers_liquid():
+    """all-liquid tank: the trailing face becomes liquid, the leading face obstacle"""
+    n = 10
+    flags, fill, rho = _moving_box_scene(n)
+    box = I.Box(center=(4.4999, 5.0, 5.0), half=(2.0, 2.0, 2.0), density_ratio=1e6, vel=(2e-4, 0.0, 0.0),
+                mode=I.MODE_FREE)
+    s = _sim(n, flags, fill, rho, [box])
+    before = s.fields()["flags"].reshape(n, n, n)
+    exp0 = flags.copy()
+    exp0[3:7, 3:7, 2:6] = O_
+    assert np.array_equal(before, exp0)
+    s.step(1)
+    got = s.fields()["flags"].reshape(n, n, n)
+    exp1 = flags.copy()
+    exp1[3:7, 3:7, 3:7] = O_
+    assert np.array_equal(got, exp1)
+    L = s.ledger()
+    assert abs(L["covered"] - 16.0) < 1e-2 and abs(L["uncovered"] - 16.0) < 1e-2
+    assert _ledger_ok(s)
+
+
+def test_box_moving_through_surface_uncovers_liquid_interface_gas():
+    """box straddling the surface: below the surface an uncovered cell sees no
+    gas (-> liquid), at the surface level liquid and gas (-> interface), above
+    it no liquid (-> gas)"""
+    n = 12
+    flags, fill, rho = _moving_box_scene(n, z_surface=6)
+    # faces kept off the cell centres: a face through a centre is a tie that
+    # the tiny rotation from the surface torque would decide
+    box = I.Box(center=(4.4999, 6.0, 6.5), half=(2.0, 2.0, 1.9), density_ratio=1e6, vel=(2e-4, 0.0, 0.0),
+                mode=I.MODE_FREE)
+    s = _sim(n, flags, fill, rho, [box])
+    s.step(1)
+    got = s.fields()["flags"].reshape(n, n, n)
+    exp = flags.copy()
+    exp[5:8, 4:8, 3:7] = O_       # box at its new pose (x cells 3..6, y 4..7, z 5..7)
+    exp[5, 4:8, 2] = L_           # uncovered column x = 2
+    exp[6, 4:8, 2] = I_
+    exp[7, 4:8, 2] = G_
+    assert np.array_equal(got, exp)
+    fl = s.fields()["fill"].reshape(n, n, n)
+    assert np.all(np.abs(fl[6, 4:8, 2] - 0.5) < 0.05)
+    assert _ledger_ok(s)
