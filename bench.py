@@ -1,0 +1,307 @@
+"""Throughput of the free-surface LBM step on GB300: MLUPS and HBM-roofline
+fraction of the bulk stream-collide kernel, FP32 / FP16-shifted storage next
+to the plain FP64 path, on the 768 x 384 x 256 wave tank with 16 free boxes.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  'value' is the FP32-storage MLUPS (all
+cells, whole job); the FP16 and FP64 runs of the same workload are reported
+under 'variants'.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline, FP32/FP16-stored vs FP64 plain at stated error"
+BYTES_PER_FLUID = {"f64": 38 * 8, "f32": 38 * 4, "f16s": 80}
+DTYPE = {"f64": "f64", "f32": "f32", "f16s": "f16s/f32"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        rows = []
+        try:
+            with open(self.out.name) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def fluid_counts(sim):
+    f = sim.fields()
+    fl = f["flags"]
+    return int(((fl == 1) | (fl == 2)).sum()), int((fl == 1).sum()), int((fl == 2).sum())
+
+
+def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=None):
+    import torch
+
+    from paper_1201_0351_gb300 import lbm_fs
+
+    sim = lbm_fs.Simulation(sc, storage=storage, use_graphs=True)
+    sim.step(warmup)
+    sim.sync()
+    n_fluid0, n_liq0, n_if0 = fluid_counts(sim)
+    launches0 = sim.stats()["kernel_launches"]
+    stream = sim.stream
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    ctx = clocks if clocks is not None else _Null()
+    with ctx:
+        start.record(stream)
+        sim.step(steps)
+        end.record(stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    ms = start.elapsed_time(end)
+    st = sim.stats()
+    launches = st["kernel_launches"] - launches0
+    n_fluid1, n_liq1, n_if1 = fluid_counts(sim)
+    kt = sim.kernel_times(kernel_steps)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    n = sc.nx * sc.ny * sc.nz
+    n_liq = 0.5 * (n_liq0 + n_liq1)
+    n_if = 0.5 * (n_if0 + n_if1)
+    b_fluid = BYTES_PER_FLUID[storage]
+    step_bytes = (n_liq + n_if) * b_fluid + n * 1 + n_if * 24
+    liquid_bytes = n_liq * b_fluid + n * 1
+    total_k = sum(kt.values())
+    return dict(storage=storage, ms_total=ms, ms_per_step=ms / steps, mlups=n * steps / (ms * 1e-3) / 1e6,
+                fluid_mlups=(n_liq + n_if) * steps / (ms * 1e-3) / 1e6, step_gbs=step_bytes / (ms / steps * 1e-3) / 1e9,
+                liquid_ms=kt.get("liquid", float("nan")) / kernel_steps, liquid_bytes=liquid_bytes,
+                liquid_gbs=liquid_bytes / (kt.get("liquid", float("nan")) / kernel_steps * 1e-3) / 1e9,
+                kernel_share={k: v / total_k for k, v in kt.items() if total_k > 0},
+                launches=launches, status=st["status"], n_fluid=(n_liq + n_if), n_interface=n_if,
+                mass_resid=(st["liquid_mass"] - st["mass0"] - (st["uncovered"] - st["covered"] - st["lost_excess"]))
+                / st["mass0"])
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def e2e_run(sc, storage, steps):
+    """Through the public API with host buffers: create (uploads the initial
+    host arrays), then every step lbm_fs_step + lbm_fs_forces of all bodies
+    (device -> host read of the step's result), timed on the host clock."""
+    import torch
+
+    from paper_1201_0351_gb300 import lbm_fs
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = lbm_fs.Simulation(sc, storage=storage, use_graphs=True, host_init=True)
+    for _ in range(steps):
+        sim.step(1)
+        for b in range(sim.nbodies):
+            lbm_fs.lbm_fs_forces(sim.h, b)
+    sim.sync()
+    t1 = time.perf_counter()
+    sim.close()
+    n = sc.nx * sc.ny * sc.nz
+    h2d = sc.flags.nbytes + sc.fill.nbytes + sc.rho.nbytes
+    d2h = sim.nbodies * 8 * (3 + 3 + 3 + 4)
+    return dict(value=n * steps / (t1 - t0) / 1e6, unit="MLUPS", h2d_bytes_per_step=h2d // steps,
+                d2h_bytes_per_step=d2h)
+
+
+def cpu_baseline(sc_full, target_s=15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: a 192 x 96 column-crop of the tank (full depth, walls on the cut),
+    as many steps as fit in about target_s seconds."""
+    import oracle
+    from paper_1201_0351_gb300 import inputs
+
+    sc = inputs.crop(sc_full, min(192, sc_full.nx), min(96, sc_full.ny))
+    t0 = time.perf_counter()
+    sim = oracle.OracleSim(sc)
+    t_setup = time.perf_counter() - t0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > target_s or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    n = sc.nx * sc.ny * sc.nz
+    return dict(value=n * steps / dt / 1e6, unit="MLUPS", cores=1, kind="oracle",
+                sample="%dx%dx%d crop of the wave tank, %d boxes, %d steps, %.1f s (setup %.1f s)" % (
+                    sc.nx, sc.ny, sc.nz, len(sc.boxes), steps, dt, t_setup))
+
+
+def workload(args):
+    from paper_1201_0351_gb300 import inputs
+
+    return inputs.wave_tank(args.nx, args.ny, args.nz, nboxes=args.boxes)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=768)
+    ap.add_argument("--ny", type=int, default=384)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--boxes", type=int, default=16)
+    ap.add_argument("--f64-steps", type=int, default=0, help="steps of the FP64 variant (default steps // 10)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_info()
+    config = {"workload": "wave tank %dx%dx%d, %d free boxes 24x12x8, tau 0.52, g 1e-5" % (
+        args.nx, args.ny, args.nz, args.boxes), "grid": [args.nx, args.ny, args.nz], "cells": args.nx * args.ny * args.nz,
+        "l2": "inputs larger than L2 (>= 5.7 GB per population grid)", "parallelism": "replicas" if ws > 1 else "1 GPU"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        sc = workload(args)
+        cb = cpu_baseline(sc, target_s=max(5.0, min(60.0, 2.0 * (args.steps + args.warmup))))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                             "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        barrier = dist.barrier
+    else:
+        torch.cuda.set_device(0)
+        barrier = None
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sc = workload(args)
+    clocks = ClockSampler(local)
+    main_run = run_storage(sc, "f32", args.steps, max(args.warmup, 3), 5, clocks=clocks, barrier=barrier)
+    variants = {}
+    if not args.no_variants:
+        variants["f16s"] = run_storage(sc, "f16s", args.steps, max(args.warmup, 3), 5, barrier=barrier)
+        f64_steps = args.f64_steps or max(3, args.steps // 10)
+        variants["f64"] = run_storage(sc, "f64", f64_steps, 3, 2, barrier=barrier)
+    ms = main_run["ms_total"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n = sc.nx * sc.ny * sc.nz
+    value = ws * n * args.steps / (ms * 1e-3) / 1e6
+    e2e = e2e_run(sc, "f32", max(10, min(args.steps, 50)))
+    e2e["value"] *= ws
+    if rank != 0:
+        return 0
+    cb = None if args.no_cpu else cpu_baseline(sc)
+    frac = main_run["liquid_gbs"] / hbm
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "kernel": "k_liquid (stream + collide of liquid cells)",
+                     "achieved": main_run["liquid_gbs"], "peak": hbm, "unit": "GB/s", "frac": frac,
+                     "peak_source": peak_src, "traffic": None,
+                     "algorithmic_bytes_per_launch": main_run["liquid_bytes"],
+                     "step_achieved_gbs": main_run["step_gbs"], "step_frac": main_run["step_gbs"] / hbm},
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": main_run["launches"], "clocks": clocks.summary(),
+        "fluid_mlups": main_run["fluid_mlups"], "kernel_share": main_run["kernel_share"],
+        "mass_drift_per_step": main_run["mass_resid"] / (args.steps + max(args.warmup, 3)),
+        "variants": {k: {kk: v[kk] for kk in ("mlups", "ms_per_step", "liquid_gbs", "step_gbs", "launches",
+                                               "mass_resid")} | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k]}
+                     for k, v in variants.items()},
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

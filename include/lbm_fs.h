@@ -1,0 +1,194 @@
+/*
+ * lbm_fs.h -- C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann
+ * library with floating rigid boxes.
+ *
+ * Method: Bogner & Ruede, "Liquid-gas-solid flows with lattice Boltzmann:
+ * Simulation of floating bodies" (arXiv:1201.0351).  One time step is the
+ * D3Q19 BGK stream + collide with gravity (Sec. 2.1, Eqs. lbgk, equilibrium,
+ * forceterm), the free-surface boundary with interface mass exchange and
+ * atmosphere reconstruction (Sec. 2.2, Eq. reconstruct), moving-wall bounce-back
+ * at obstacle links with the momentum-exchange force and torque on each box
+ * (Sec. 2.3, Eqs. noslip, momentumexchange, netforce, torque; Sec. 2.4, Eq.
+ * momentuminterface), the interface cell conversions (Sec. 2.2), the rigid-body
+ * update, and the obstacle remapping with the obstacle-to-fluid rule (Sec. 2.4).
+ *
+ * Conventions (all quantities in lattice units):
+ *  - grid nx x ny x nz; cell (x,y,z) is [x,x+1]x[y,y+1]x[z,z+1] (Sec. 2.1);
+ *    linear index idx = x + nx*(y + ny*z);
+ *  - cell classes: 1 liquid, 2 interface, 4 gas, 8 obstacle;
+ *  - a non-periodic face is a resting no-slip wall half a cell outside the grid;
+ *  - populations are numbered C,W,E,N,S,T,B,TW,TE,TN,TS,NW,NE,SW,SE,BW,BE,BN,BS
+ *    (the order of the paper's D3Q19 stencil figure).
+ *
+ * Errors: every call returns an lbm_fs_status; nothing is thrown across the
+ * ABI.  Invalid arguments give LBM_FS_EINVAL before any allocation.  Device-side
+ * conditions (a liquid cell touching gas, a non-finite density, a worklist
+ * overflow) are sticky bits in a device status word; they are reported as
+ * LBM_FS_EUNSTABLE / LBM_FS_EOVERFLOW by the next call that synchronises
+ * (lbm_fs_forces, lbm_fs_body_state, lbm_fs_read_fields, lbm_fs_stats,
+ * lbm_fs_sync).  lbm_fs_last_error_string() describes the last failure of the
+ * calling thread.  A handle may be used by one host thread at a time; distinct
+ * handles are independent.
+ */
+#ifndef LBM_FS_H
+#define LBM_FS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_fs lbm_fs; /* opaque; owned by the library */
+
+typedef enum {
+    LBM_FS_OK = 0,
+    LBM_FS_EINVAL = -1,    /* invalid argument or parameter */
+    LBM_FS_ENOMEM = -2,    /* device allocation failed */
+    LBM_FS_ECUDA = -3,     /* a CUDA runtime call failed */
+    LBM_FS_ESTATE = -4,    /* call not valid in the handle's state */
+    LBM_FS_EUNSTABLE = -5, /* non-finite density, or liquid touching gas */
+    LBM_FS_ETIMEOUT = -6,  /* reserved: a bounded device wait gave up */
+    LBM_FS_EOVERFLOW = -7  /* a device worklist overflowed */
+} lbm_fs_status;
+
+/* population storage precision */
+enum {
+    LBM_FS_F64 = 0,  /* f_q as double; arithmetic in double (the plain path) */
+    LBM_FS_F32 = 1,  /* f_q - w_q as float; arithmetic in float */
+    LBM_FS_F16S = 2  /* f_q - w_q as half (q >= 1, scaled by 2^10) plus a float
+                        rest population that makes the stored cell sum equal the
+                        collision density; arithmetic in float */
+};
+
+/* cell classes (init_flags input and LBM_FS_FIELD_FLAGS output) */
+enum { LBM_FS_LIQUID = 1, LBM_FS_INTERFACE = 2, LBM_FS_GAS = 4, LBM_FS_OBSTACLE = 8 };
+
+/* box motion modes (lbm_fs_box.mode) */
+enum {
+    LBM_FS_MODE_FIXED = 0,         /* held at its pose, velocity zero */
+    LBM_FS_MODE_FREE = 1,          /* 6 degrees of freedom */
+    LBM_FS_MODE_ROT_AXIS_ONLY = 2, /* translation + rotation about rot_axis only */
+    LBM_FS_MODE_DAMP_TRANSLATION = 0x100 /* flag: v *= (1 - lin_damping) each step */
+};
+
+typedef struct {
+    int32_t nx, ny, nz;
+    uint32_t periodic;     /* bit0 x, bit1 y, bit2 z; other faces are walls */
+    double tau;            /* BGK relaxation time, > 1/2 (tau = 3 nu + 1/2) */
+    double gravity[3];     /* acceleration on liquid and bodies */
+    double body_accel[3];  /* extra acceleration on the liquid only */
+    double rho_gas;        /* gas density rho_G = 3 p_G (Eq. pressure) */
+    double eps;            /* conversion threshold: fill at phi >= 1+eps, empty at phi <= -eps */
+    int32_t storage;       /* LBM_FS_F64 / LBM_FS_F32 / LBM_FS_F16S */
+    /* initial state, nx*ny*nz entries each (3 per cell for init_vel, xyz):
+     * classes 1/2/4, fill level, density, velocity (NULL = at rest).  Fluid cells
+     * start at f = f_eq(rho, u).  The arrays are copied; the caller keeps them.
+     * init_flags, init_fill and init_rho are required. */
+    const uint8_t *init_flags;
+    const double *init_fill;
+    const double *init_rho;
+    const double *init_vel;
+    int32_t init_on_device; /* nonzero: the four init pointers are device pointers */
+    /* device memory: dev_alloc / dev_free with alloc_ctx (e.g. a framework's
+     * caching allocator); NULL -> cudaMalloc / cudaFree */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+    void *stream;          /* cudaStream_t for all work; NULL -> legacy default stream */
+    int32_t use_graphs;    /* nonzero: steps replay a captured CUDA graph */
+} lbm_fs_params;
+
+typedef struct {
+    double center[3];      /* centre of mass (world) */
+    double half[3];        /* half extents along the body axes */
+    double quat[4];        /* (w, x, y, z), body -> world */
+    double density_ratio;  /* body density / liquid density */
+    double vel[3];         /* initial velocity */
+    double omega[3];       /* initial angular velocity (world) */
+    int32_t mode;          /* LBM_FS_MODE_* */
+    double rot_axis[3];    /* unit axis (world) for LBM_FS_MODE_ROT_AXIS_ONLY */
+    double lin_damping;    /* for LBM_FS_MODE_DAMP_TRANSLATION */
+} lbm_fs_box;
+
+typedef struct {
+    double F[3], T[3];     /* force and torque of the last step (Eqs. netforce, torque) */
+    double S;              /* sum of |link terms| (scale of F for tolerances) */
+    double center[3], quat[4], vel[3], omega[3];
+} lbm_fs_body_state_t;
+
+typedef struct {
+    int64_t step;
+    double liquid_mass;    /* sum over liquid rho + interface m (computed by this call) */
+    double mass0;          /* liquid mass at the first step */
+    double covered, uncovered, lost_excess; /* mass ledger */
+    int64_t n_interface, n_filled, n_emptied, n_new_from_gas, n_new_from_liquid, n_pending;
+    uint32_t status;       /* sticky device status bits */
+    int64_t kernel_launches; /* kernels launched by this handle so far */
+} lbm_fs_stats_t;
+
+/* field selectors for lbm_fs_read_fields / lbm_fs_write_fields; dst[k] is the
+ * buffer for bit k.  Layouts: FLAGS uint8[N]; FILL, MASS, RHO double[N];
+ * VEL double[3N] (xyz per cell); F double[19N] (SoA, [q][idx]).  FILL is 1 for
+ * liquid, phi for interface, 0 else; MASS is rho / m / 0; RHO and VEL are the
+ * density and the velocity of the last collision (sum c f / rho - a) of liquid
+ * and interface cells, 0 else; F is 0 outside liquid and interface cells. */
+enum {
+    LBM_FS_FIELD_FLAGS = 1u << 0,
+    LBM_FS_FIELD_FILL = 1u << 1,
+    LBM_FS_FIELD_MASS = 1u << 2,
+    LBM_FS_FIELD_RHO = 1u << 3,
+    LBM_FS_FIELD_VEL = 1u << 4,
+    LBM_FS_FIELD_F = 1u << 5
+};
+
+/* Creates a simulation (Sec. 2.1 grid, Sec. 2.2 initial fill).  Validates the
+ * parameters (tau > 1/2, sizes, storage, the incompressibility bound of Sec.
+ * 2.1: (nx, ny, nz) . |g| < 1/3), allocates the device state and uploads the
+ * initial fields.  On success *out owns all device memory until
+ * lbm_fs_destroy. */
+lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out);
+lbm_fs_status lbm_fs_destroy(lbm_fs *h);
+
+/* Adds a rigid box and maps it to the lattice: a cell is an obstacle iff its
+ * centre lies strictly inside the box (Sec. 2.3).  Before the first step the
+ * covered mass is excluded from the initial mass; between steps it is booked as
+ * covered.  At most 255 boxes. *out_id receives the body id (may be NULL). */
+lbm_fs_status lbm_fs_add_box(lbm_fs *h, const lbm_fs_box *b, int32_t *out_id);
+
+/* Enqueues nsteps time steps on the handle's stream and returns without
+ * waiting. */
+lbm_fs_status lbm_fs_step(lbm_fs *h, int32_t nsteps);
+
+/* Synchronises and returns the force and torque of the last step on body id
+ * and its current pose.  Any pointer may be NULL. */
+lbm_fs_status lbm_fs_forces(lbm_fs *h, int32_t id, double F[3], double T[3],
+                            double center[3], double quat[4]);
+lbm_fs_status lbm_fs_body_state(lbm_fs *h, int32_t id, lbm_fs_body_state_t *out);
+
+/* Synchronises and copies the selected fields into caller-owned buffers (host
+ * or device, per dst_on_device), each sized as documented above. */
+lbm_fs_status lbm_fs_read_fields(lbm_fs *h, uint32_t mask, void *const *dst,
+                                 int32_t dst_on_device);
+
+/* Synchronises and fills *out (computes the current liquid mass on the device). */
+lbm_fs_status lbm_fs_stats(lbm_fs *h, lbm_fs_stats_t *out);
+
+/* Synchronises the handle's stream and reports sticky device errors. */
+lbm_fs_status lbm_fs_sync(lbm_fs *h);
+
+/* Runs nsteps steps without graphs, timing every kernel with CUDA events on the
+ * handle's stream; ms[k] receives the summed milliseconds of kernel k over the
+ * steps and names (may be NULL) a static name per kernel.  Returns the number
+ * of kernels in *nk (at most cap entries are written). */
+lbm_fs_status lbm_fs_kernel_times(lbm_fs *h, int32_t nsteps, double *ms,
+                                  const char **names, int32_t cap, int32_t *nk);
+
+const char *lbm_fs_last_error_string(void);
+int32_t lbm_fs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_FS_H */

@@ -1,0 +1,80 @@
+// Internal declarations shared by the host API and the kernel translation
+// units of the free-surface LBM library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmfs {
+
+constexpr int Q = 19;
+constexpr int MAX_BODIES = 255;
+constexpr int FORCE_BLOCKS = 64;   // blocks per body in the force / remap kernels
+constexpr int LIST_BLOCKS = 304;   // 2 x 152 SMs: grid of the worklist kernels
+constexpr int LIST_THREADS = 256;
+constexpr int REMAP_THREADS = 512;
+constexpr int BULK_THREADS = 128;  // x extent of a bulk-kernel block
+
+// cell classes (as in the C ABI)
+enum : uint8_t { CL_L = 1, CL_I = 2, CL_G = 4, CL_O = 8 };
+// per-cell conversion marks (separate byte array, zero between steps)
+enum : uint8_t {
+    MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_PEND = 32, MK_FRESH = 64
+};
+// sticky device status bits
+enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
+
+// worklists
+enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COUNT };
+// ledger slots (double)
+enum { LG_COVERED = 0, LG_UNCOVERED, LG_LOST, LG_MASS0, LG_MASS, LG_COUNT };
+
+struct Body {
+    double o[3], h[3], q[4], dens, v[3], w[3], axis[3], damp;
+    double dv[3], dw[3];
+    double F[3], T[3], S;
+    double R[9];        // rotation of q (row-major), recomputed with the pose
+    int mode, pad;
+    int lo[3], hi[3];   // cells that may be inside at the current pose, [lo, hi)
+    int plo[3], phi[3]; // the same at the previous pose
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    int nx, ny, nz;
+    unsigned periodic;
+    long long N;
+    double omega, a[3], grav[3], rho_g, eps;
+    uint8_t *flags, *bid, *cmark;
+    void *fsrc, *fdst;
+    double *phisrc, *phidst, *m;
+    uint32_t *list[WL_COUNT];
+    uint32_t *cnt;  // WL_COUNT counters
+    uint32_t cap;
+    Body *bodies;
+    int nb;
+    double *part;   // nb * FORCE_BLOCKS * 7
+    double *ledger; // LG_COUNT
+    uint32_t *status;
+    uint8_t *rdec;  // remap scratch: decision per pending item
+    double *rrho, *rphi;
+    double *red;    // reduction scratch
+};
+
+struct KernelSet {
+    void (*init_cells)(const Dev &, const uint8_t *flags, const double *fill, const double *rho, const double *vel,
+                       cudaStream_t);
+    void (*body_prepare)(const Dev &, int b, cudaStream_t);
+    void (*map_body)(const Dev &, int b, int book_mass, cudaStream_t);
+    // one time step, in order; returns the number of kernels launched
+    int (*step)(const Dev &, cudaStream_t, float *ev_ms, cudaEvent_t *ev);
+    void (*liquid_mass)(const Dev &, cudaStream_t);  // -> ledger[LG_MASS]
+    void (*read_fields)(const Dev &, unsigned mask, void *const *dst, cudaStream_t);
+    int nkernels;
+    const char *const *names;
+};
+
+KernelSet kernels_f64();
+KernelSet kernels_f32();
+KernelSet kernels_f16s();
+
+}  // namespace lbmfs

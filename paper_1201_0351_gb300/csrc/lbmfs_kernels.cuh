@@ -1,0 +1,1398 @@
+// Device code of the free-surface LBM step (Bogner & Ruede, Sec. 2), templated
+// on the population storage.  Included by one translation unit per storage:
+//   S = 0  f_q as double, double arithmetic.  Every operation is written in the
+//          same order as the plain CPU restatement of the method and the unit is
+//          compiled with -fmad=false, so this path reproduces it bit for bit
+//          (except for the order of the parallel force / ledger sums);
+//   S = 1  f_q - w_q as float, float arithmetic on deviations;
+//   S = 2  f_q - w_q as half (q >= 1, times 2^10) with a float rest population
+//          chosen so that the stored cell sum equals the collision density.
+// Interface mass, fill level, forces, torques and the ledger are double in all
+// three.
+#pragma once
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lbmfs_internal.h"
+
+namespace lbmfs {
+namespace {  // internal linkage: one copy per storage translation unit
+
+// ----------------------------------------------------------------- lattice
+// D3Q19 in the order C,W,E,N,S,T,B,TW,TE,TN,TS,NW,NE,SW,SE,BW,BE,BN,BS (the
+// order of the paper's stencil figure, Eq. links).
+__host__ __device__ __forceinline__ constexpr int cx(int q) {
+    return q == 1 || q == 7 || q == 11 || q == 13 || q == 15 ? -1
+           : (q == 2 || q == 8 || q == 12 || q == 14 || q == 16 ? 1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int cy(int q) {
+    return q == 3 || q == 9 || q == 11 || q == 12 || q == 17 ? 1
+           : (q == 4 || q == 10 || q == 13 || q == 14 || q == 18 ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int cz(int q) {
+    return q == 5 || (q >= 7 && q <= 10) ? 1 : (q == 6 || q >= 15 ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int opp(int q) {
+    // C-C, W-E, N-S, T-B, TW-BE, TE-BW, TN-BS, TS-BN, NW-SE, NE-SW
+    return q == 0 ? 0
+                  : (q <= 6 ? (q & 1 ? q + 1 : q - 1)
+                            : (q == 7 || q == 8 || q == 15 || q == 16 ? 23 - q
+                                                                      : (q <= 14 && q >= 11 ? 25 - q : 27 - q)));
+}
+// the table is checked at compile time: c_opp(q) = -c_q, weights symmetric
+__host__ __device__ constexpr bool lattice_ok() {
+    for (int q = 0; q < 19; ++q) {
+        int p = opp(q);
+        if (cx(p) != -cx(q) || cy(p) != -cy(q) || cz(p) != -cz(q)) return false;
+        int s = (cx(q) != 0) + (cy(q) != 0) + (cz(q) != 0);
+        if ((q == 0) != (s == 0) || (q >= 1 && q <= 6) != (s == 1) || (q >= 7) != (s == 2)) return false;
+    }
+    return true;
+}
+static_assert(lattice_ok(), "D3Q19 table");
+// weights of the stencil figure caption: 1/3, 1/18, 1/36
+__host__ __device__ __forceinline__ constexpr double wd(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+__host__ __device__ __forceinline__ constexpr float wf(int q) {
+    return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+constexpr double NORMAL_DEADBAND = 1e-6;  // Eq. reconstruct: c.n < -1e-6
+constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2015
+constexpr float F16_SCALE = 1024.0f;
+constexpr float F16_INV_SCALE = 1.0f / 1024.0f;
+constexpr int CL_WALL = 256;
+
+// ----------------------------------------------------------------- storage
+template <int S> struct Sto;
+
+template <> struct Sto<0> {
+    using R = double;
+    static constexpr bool shifted = false;
+    static __device__ __forceinline__ double ld(const void *g, int q, long long i, long long N) {
+        return reinterpret_cast<const double *>(g)[(long long)q * N + i];
+    }
+    static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, double v) {
+        reinterpret_cast<double *>(g)[(long long)q * N + i] = v;
+    }
+    // value of f_q as double
+    static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
+        return ld(g, q, i, N);
+    }
+    // store a full cell given as 19 doubles f_q
+    static __device__ __forceinline__ void st_cell(void *g, long long i, long long N, const double *f) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) st(g, q, i, N, f[q]);
+    }
+    static size_t bytes(long long N) { return (size_t)N * Q * sizeof(double); }
+};
+
+template <> struct Sto<1> {
+    using R = float;
+    static constexpr bool shifted = true;
+    static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
+        return reinterpret_cast<const float *>(g)[(long long)q * N + i];
+    }
+    static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, float v) {
+        reinterpret_cast<float *>(g)[(long long)q * N + i] = v;
+    }
+    static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
+        return wd(q) + (double)ld(g, q, i, N);
+    }
+    static __device__ __forceinline__ void st_cell(void *g, long long i, long long N, const double *f) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) st(g, q, i, N, (float)(f[q] - wd(q)));
+    }
+    // store deviations d_q; drho = collision density - 1 (unused for float)
+    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, float) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) st(g, q, i, N, dv[q]);
+    }
+    static size_t bytes(long long N) { return (size_t)N * Q * sizeof(float); }
+};
+
+template <> struct Sto<2> {
+    using R = float;
+    static constexpr bool shifted = true;
+    // plane 0: float (N); planes 1..18: half (N each), after it
+    static __device__ __forceinline__ const __half *hp(const void *g, long long N) {
+        return reinterpret_cast<const __half *>(reinterpret_cast<const float *>(g) + N);
+    }
+    static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
+        if (q == 0) return reinterpret_cast<const float *>(g)[i];
+        return __half2float(hp(g, N)[(long long)(q - 1) * N + i]) * F16_INV_SCALE;
+    }
+    static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
+        return wd(q) + (double)ld(g, q, i, N);
+    }
+    // d*_q for q >= 1 rounded to half; the rest population takes
+    // (rho - 1) - sum_{q>=1} dequant(h_q) so that the stored sum is rho
+    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, float drho) {
+        __half *h = const_cast<__half *>(hp(g, N));
+        float rest = drho;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            __half hq = __float2half_rn(dv[q] * F16_SCALE);
+            h[(long long)(q - 1) * N + i] = hq;
+            rest -= __half2float(hq) * F16_INV_SCALE;
+        }
+        reinterpret_cast<float *>(g)[i] = rest;
+    }
+    static __device__ __forceinline__ void st_cell(void *g, long long i, long long N, const double *f) {
+        double drho = 0.0;
+        float dv[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double d = f[q] - wd(q);
+            drho += d;
+            dv[q] = (float)d;
+        }
+        st_dev(g, i, N, dv, (float)drho);
+    }
+    static size_t bytes(long long N) { return (size_t)N * (sizeof(float) + (Q - 1) * sizeof(__half)); }
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ long long nbr(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
+    int px = x + dx, py = y + dy, pz = z + dz;
+    if (px < 0 || px >= d.nx) {
+        if (!(d.periodic & 1u)) return -1;
+        px = px < 0 ? px + d.nx : px - d.nx;
+    }
+    if (py < 0 || py >= d.ny) {
+        if (!(d.periodic & 2u)) return -1;
+        py = py < 0 ? py + d.ny : py - d.ny;
+    }
+    if (pz < 0 || pz >= d.nz) {
+        if (!(d.periodic & 4u)) return -1;
+        pz = pz < 0 ? pz + d.nz : pz - d.nz;
+    }
+    return px + (long long)d.nx * (py + (long long)d.ny * pz);
+}
+
+__device__ __forceinline__ void coords(const Dev &d, long long idx, int &x, int &y, int &z) {
+    x = (int)(idx % d.nx);
+    long long r = idx / d.nx;
+    y = (int)(r % d.ny);
+    z = (int)(r / d.ny);
+}
+
+__device__ __forceinline__ int cls(const Dev &d, long long i) { return i < 0 ? CL_WALL : (int)d.flags[i]; }
+
+// warp-aggregated append of val to a worklist
+__device__ __forceinline__ void wl_append(const Dev &d, bool pred, int list, uint32_t val) {
+    unsigned act = __activemask();
+    unsigned mask = __ballot_sync(act, pred);
+    if (!pred) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&d.cnt[list], (uint32_t)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    uint32_t pos = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+    if (pos < d.cap) d.list[list][pos] = val;
+    else atomicOr(d.status, ST_OVERFLOW);
+}
+
+__device__ __forceinline__ uint32_t wl_count(const Dev &d, int list) {
+    uint32_t c = *reinterpret_cast<volatile uint32_t *>(&d.cnt[list]);
+    return c < d.cap ? c : d.cap;
+}
+
+// atomic OR / AND on one byte of the mark array; returns the old byte
+__device__ __forceinline__ uint8_t mark_or(const Dev &d, long long i, uint8_t bits) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(d.cmark + i);
+    unsigned int *w = reinterpret_cast<unsigned int *>(a & ~(uintptr_t)3);
+    unsigned sh = (unsigned)(a & 3) * 8u;
+    unsigned old = atomicOr(w, (unsigned)bits << sh);
+    return (uint8_t)(old >> sh);
+}
+__device__ __forceinline__ void mark_and(const Dev &d, long long i, uint8_t bits) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(d.cmark + i);
+    unsigned int *w = reinterpret_cast<unsigned int *>(a & ~(uintptr_t)3);
+    unsigned sh = (unsigned)(a & 3) * 8u;
+    atomicAnd(w, ~((unsigned)bits << sh));
+}
+
+__device__ __forceinline__ double min_image(const Dev &d, double v, int k) {
+    if (d.periodic & (1u << k)) {
+        double n = k == 0 ? (double)d.nx : (k == 1 ? (double)d.ny : (double)d.nz);
+        v = v - n * floor(v / n + 0.5);
+    }
+    return v;
+}
+
+// rotation matrix of the unit quaternion (w, x, y, z), row-major
+__device__ __forceinline__ void rotation(const double *q, double *R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// Sec. 2.3: cell centre strictly inside the box
+__device__ __forceinline__ bool inside(const Dev &d, const Body &b, int x, int y, int z) {
+    double dd[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
+                    min_image(d, (z + 0.5) - b.o[2], 2)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double bk = (b.R[0 * 3 + k] * dd[0] + b.R[1 * 3 + k] * dd[1]) + b.R[2 * 3 + k] * dd[2];
+        if (!(fabs(bk) < b.h[k])) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void body_velocity_at(const Dev &d, const Body &b, const double *p, double *uw) {
+    double r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = min_image(d, p[k] - b.o[k], k);
+    double c0 = b.w[1] * r[2] - b.w[2] * r[1];
+    double c1 = b.w[2] * r[0] - b.w[0] * r[2];
+    double c2 = b.w[0] * r[1] - b.w[1] * r[0];
+    uw[0] = b.v[0] + c0;
+    uw[1] = b.v[1] + c1;
+    uw[2] = b.v[2] + c2;
+}
+
+// c_q . u_w with u_w at the midpoint x_c + c_qbar / 2 of the link (x, q)
+__device__ __forceinline__ double link_cuw(const Dev &d, const Body &b, int x, int y, int z, int q) {
+    int qb = opp(q);
+    double p[3] = {(x + 0.5) + 0.5 * cx(qb), (y + 0.5) + 0.5 * cy(qb), (z + 0.5) + 0.5 * cz(qb)};
+    double uw[3];
+    body_velocity_at(d, b, p, uw);
+    return (cx(q) * uw[0] + cy(q) * uw[1]) + cz(q) * uw[2];
+}
+
+// ------------------------------------------------- double arithmetic (Sec. 2.1)
+
+// Eq. equilibrium, c_s^2 = 1/3
+__device__ __forceinline__ double feq_d(int q, double rho, const double *u) {
+    double cu = (cx(q) * u[0] + cy(q) * u[1]) + cz(q) * u[2];
+    double usq = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    double t = ((1.0 + 3.0 * cu) + (4.5 * cu) * cu) - 1.5 * usq;
+    return (wd(q) * rho) * t;
+}
+
+// Eq. forceterm (Luo): w rho [3 (c - u) + 9 (c.u) c] . a
+__device__ __forceinline__ double force_d(int q, double rho, const double *u, const double *a) {
+    double cu = (cx(q) * u[0] + cy(q) * u[1]) + cz(q) * u[2];
+    double tx = (3.0 * (cx(q) - u[0]) + (9.0 * cu) * cx(q)) * a[0];
+    double ty = (3.0 * (cy(q) - u[1]) + (9.0 * cu) * cy(q)) * a[1];
+    double tz = (3.0 * (cz(q) - u[2]) + (9.0 * cu) * cz(q)) * a[2];
+    return (wd(q) * rho) * ((tx + ty) + tz);
+}
+
+template <int S>
+__device__ __forceinline__ double cell_density(const Dev &d, const void *g, long long i) {
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) r += Sto<S>::ldf(g, q, i, d.N);
+    return r;
+}
+
+// density and the velocity of the last collision, sum c f / rho - a
+template <int S>
+__device__ __forceinline__ double cell_rho_u(const Dev &d, const void *g, long long i, double *u) {
+    double f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = Sto<S>::ldf(g, q, i, d.N);
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) r += f[q];
+    double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        j0 += cx(q) * f[q];
+        j1 += cy(q) * f[q];
+        j2 += cz(q) * f[q];
+    }
+    u[0] = j0 / r - d.a[0];
+    u[1] = j1 / r - d.a[1];
+    u[2] = j2 / r - d.a[2];
+    return r;
+}
+
+// double BGK collision of the post-stream cell fp -> fnew (Eq. lbgk, R1 order)
+__device__ __forceinline__ void collide_d(const Dev &d, const double *fp, double *fnew) {
+    double rho = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) rho += fp[q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        j0 += cx(q) * fp[q];
+        j1 += cy(q) * fp[q];
+        j2 += cz(q) * fp[q];
+    }
+    double u[3] = {j0 / rho, j1 / rho, j2 / rho};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        double fe = feq_d(q, rho, u);
+        double fq = force_d(q, rho, u, d.a);
+        fnew[q] = (fp[q] - d.omega * (fp[q] - fe)) + fq;
+    }
+}
+
+// ----------------------------------------- float arithmetic on deviations
+
+// BGK collision of deviations dp_q = f'_q - w_q -> dn_q; returns rho - 1
+__device__ __forceinline__ float collide_f(const Dev &d, const float *dp, float *dn, float &rho_out) {
+    float dr = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dr += dp[q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (cx(q)) j0 += cx(q) * dp[q];
+        if (cy(q)) j1 += cy(q) * dp[q];
+        if (cz(q)) j2 += cz(q) * dp[q];
+    }
+    float rho = 1.0f + dr;
+    float inv = 1.0f / rho;
+    float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
+    float usq = ux * ux + uy * uy + uz * uz;
+    float om = (float)d.omega;
+    float ax = (float)d.a[0], ay = (float)d.a[1], az = (float)d.a[2];
+    float ua = ux * ax + uy * ay + uz * az;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
+        float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
+        float deq = wf(q) * (dr + s + dr * s);  // w (rho (1 + s) - 1)
+        float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
+        float fq = wf(q) * rho * (3.0f * (ca - ua) + 9.0f * cu * ca);
+        dn[q] = dp[q] - om * (dp[q] - deq) + fq;
+    }
+    rho_out = rho;
+    return dr;
+}
+
+// f_eq(rho_g, u) - w as float deviation
+__device__ __forceinline__ float feq_dev_f(int q, float drg, float ux, float uy, float uz) {
+    float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
+    float usq = ux * ux + uy * uy + uz * uz;
+    float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
+    return wf(q) * (drg + s + drg * s);
+}
+
+// ------------------------------------------------------------- kernels
+
+// K0: initial populations f = f_eq(rho, u) (u = 0 unless given), interface
+// mass m = fill * sum f, fill = m / sum f
+template <int S>
+__global__ void k_init(Dev d, const uint8_t *flags, const double *fill, const double *rho, const double *vel) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    int c = flags[i];
+    d.flags[i] = (uint8_t)c;
+    d.bid[i] = 0;
+    d.cmark[i] = 0;
+    if (c != CL_L && c != CL_I) return;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (vel) {
+        u[0] = vel[3 * i];
+        u[1] = vel[3 * i + 1];
+        u[2] = vel[3 * i + 2];
+    }
+    double f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = feq_d(q, rho[i], u);
+    Sto<S>::st_cell(d.fsrc, i, d.N, f);
+    if (c == CL_I) {
+        double r = cell_density<S>(d, d.fsrc, i);
+        double m = fill[i] * r;
+        d.m[i] = m;
+        d.phisrc[i] = m / r;
+    }
+}
+
+// rotation matrix and the cell range that may lie inside the body
+__device__ void body_bounds(const Dev &d, Body &b) {
+    rotation(b.q, b.R);
+    int n[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        double e = (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) + fabs(b.R[k * 3 + 2]) * b.h[2];
+        int lo = (int)floor(b.o[k] - e) - 1;
+        int hi = (int)floor(b.o[k] + e) + 2;
+        if (!(d.periodic & (1u << k))) {
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > n[k] ? n[k] : hi;
+        } else if (hi - lo > n[k]) {
+            hi = lo + n[k];
+        }
+        if (hi < lo) hi = lo;
+        b.lo[k] = lo;
+        b.hi[k] = hi;
+    }
+}
+
+__global__ void k_body_prepare(Dev d, int bi) {
+    if (threadIdx.x != 0) return;
+    Body &b = d.bodies[bi];
+    body_bounds(d, b);
+    for (int k = 0; k < 3; ++k) {
+        b.plo[k] = b.lo[k];
+        b.phi[k] = b.hi[k];
+    }
+}
+
+// iterate the cells of a box range [lo, hi) (wrapped on periodic axes)
+__device__ __forceinline__ long long range_count(const int *lo, const int *hi) {
+    return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+}
+__device__ __forceinline__ void range_cell(const Dev &d, const int *lo, const int *hi, long long k, int &x, int &y,
+                                           int &z) {
+    int lx = hi[0] - lo[0], ly = hi[1] - lo[1];
+    x = lo[0] + (int)(k % lx);
+    long long r = k / lx;
+    y = lo[1] + (int)(r % ly);
+    z = lo[2] + (int)(r / ly);
+    x = ((x % d.nx) + d.nx) % d.nx;  // only periodic axes can leave [0, n)
+    y = ((y % d.ny) + d.ny) % d.ny;
+    z = ((z % d.nz) + d.nz) % d.nz;
+}
+
+// mapping of a newly added body (Sec. 2.3); book_mass: charge the covered mass
+template <int S>
+__global__ void k_map_body(Dev d, int bi, int book_mass) {
+    const Body &b = d.bodies[bi];
+    long long n = range_count(b.lo, b.hi);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        range_cell(d, b.lo, b.hi, k, x, y, z);
+        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+        int c = d.flags[i];
+        if (c == CL_O || !inside(d, b, x, y, z)) continue;
+        if (book_mass) {
+            double mass = c == CL_L ? cell_density<S>(d, d.fsrc, i) : (c == CL_I ? d.m[i] : 0.0);
+            if (mass != 0.0) atomicAdd(&d.ledger[LG_COVERED], mass);
+        }
+        d.flags[i] = CL_O;
+        d.bid[i] = (uint8_t)bi;
+    }
+}
+
+// ---- C4: momentum exchange at the links into body blockIdx.y (state at t)
+template <int S>
+__global__ void __launch_bounds__(256) k_forces(Dev d) {
+    int bi = blockIdx.y;
+    const Body &b = d.bodies[bi];
+    int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, b.lo[2] - 1};
+    int hi[3] = {b.hi[0] + 1, b.hi[1] + 1, b.hi[2] + 1};
+    int n3[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        if (!(d.periodic & (1u << k))) {
+            lo[k] = lo[k] < 0 ? 0 : lo[k];
+            hi[k] = hi[k] > n3[k] ? n3[k] : hi[k];
+        } else if (hi[k] - lo[k] > n3[k]) {
+            hi[k] = lo[k] + n3[k];
+        }
+    }
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long n = range_count(lo, hi);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        range_cell(d, lo, hi, k, x, y, z);
+        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+        int cl = d.flags[i];
+        if (cl == CL_O) continue;
+        double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
+        bool have_rho = false;
+        double rho_x = 0.0;
+        double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
+                       min_image(d, (z + 0.5) - b.o[2], 2)};
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            if (si < 0 || d.flags[si] != CL_O || d.bid[si] != bi) continue;
+            double cuw = link_cuw(d, b, x, y, z, q);
+            int qb = opp(q);
+            double inner;
+            if (cl == CL_G) {
+                inner = wd(q) * d.rho_g;
+            } else {
+                double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
+                double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
+                double C;
+                if (cuw == 0.0) {
+                    C = phi_x * 0.0;
+                } else {
+                    if (!have_rho) {
+                        rho_x = cell_density<S>(d, d.fsrc, i);
+                        have_rho = true;
+                    }
+                    C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
+                }
+                inner = (A + B) + C;
+            }
+            double g = 2.0 * inner;
+            double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+            acc[0] += F0;
+            acc[1] += F1;
+            acc[2] += F2;
+            acc[3] += r[1] * F2 - r[2] * F1;
+            acc[4] += r[2] * F0 - r[0] * F2;
+            acc[5] += r[0] * F1 - r[1] * F0;
+            acc[6] += fabs(g);
+        }
+    }
+    // deterministic block reduction (fixed shuffle tree, then warps in order)
+    __shared__ double sh[8][7];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double v = acc[c];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[wid][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        d.part[((long long)bi * FORCE_BLOCKS + blockIdx.x) * 7 + threadIdx.x] = v;
+    }
+}
+
+// ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
+template <int S>
+__global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
+    using P = Sto<S>;
+    using R = typename P::R;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y, z = blockIdx.z;
+    bool in = x < d.nx;
+    long long i = (long long)(in ? x : 0) + (long long)d.nx * (y + (long long)d.ny * z);
+    int c = in ? (int)d.flags[i] : 0;
+    wl_append(d, c == CL_I, WL_IFACE, (uint32_t)i);
+    if (c != CL_L) return;
+    const long long N = d.N;
+    const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+    const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
+    R fp[Q];
+    unsigned special = 0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        long long si = interior ? i - (cx(q) * sx + cy(q) * sy + cz(q) * sz) : nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+        int ns = si < 0 ? CL_WALL : (int)d.flags[si];
+        if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
+        else special |= 1u << q;
+    }
+    fp[0] = P::ld(d.fsrc, 0, i, N);
+    if (special) {
+        // Eq. noslip at walls and obstacles: f'_q = f*_qbar + 6 w_q rho (c_q.u_w)
+        bool have_rho = false;
+        double rho_x = 0.0;
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            if (!(special & (1u << q))) continue;
+            int qb = opp(q);
+            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            int ns = cls(d, si);
+            double cuw = 0.0;
+            if (ns == CL_O) cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
+            else if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
+            R own = P::ld(d.fsrc, qb, i, N);
+            if (cuw == 0.0) {
+                fp[q] = own;
+            } else {
+                if (!have_rho) {
+                    rho_x = cell_density<S>(d, d.fsrc, i);
+                    have_rho = true;
+                }
+                fp[q] = (R)((double)own + ((6.0 * wd(q)) * rho_x) * cuw);
+            }
+        }
+    }
+    if constexpr (!P::shifted) {
+        double fn[Q];
+        collide_d(d, fp, fn);
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            P::st(d.fdst, q, i, N, fn[q]);
+            r += fn[q];
+        }
+        if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
+    } else {
+        float dn[Q], rho;
+        float dr = collide_f(d, fp, dn, rho);
+        P::st_dev(d.fdst, i, N, dn, dr);
+        if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+    }
+}
+
+// fill level of a neighbour as seen by the normal estimate
+__device__ __forceinline__ double fill_seen(const Dev &d, long long ni, double own) {
+    int c = cls(d, ni);
+    if (c == CL_L) return 1.0;
+    if (c == CL_I) return d.phisrc[ni];
+    if (c == CL_G) return 0.0;
+    return own;
+}
+
+// ---- C1 + C2 for interface cells (Sec. 2.2): reconstruction, mass exchange
+template <int S>
+__global__ void __launch_bounds__(128) k_interface(Dev d) {
+    using P = Sto<S>;
+    const long long N = d.N;
+    uint32_t n = wl_count(d, WL_IFACE);
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        long long i = d.list[WL_IFACE][it];
+        int x, y, z;
+        coords(d, i, x, y, z);
+        long long src[Q];
+        int scl[Q];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            scl[q] = cls(d, src[q]);
+        }
+        // normal n = -grad(phi), central differences
+        double own_phi = d.phisrc[i];
+        double nv[3];
+        {
+            double pm = fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi);
+            double pp = fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi);
+            nv[0] = 0.5 * (pm - pp);
+            pm = fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi);
+            pp = fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi);
+            nv[1] = 0.5 * (pm - pp);
+            pm = fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi);
+            pp = fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi);
+            nv[2] = 0.5 * (pm - pp);
+        }
+        double m_new;
+        if constexpr (!P::shifted) {
+            double fo[Q], fp[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
+            double rho_x = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) rho_x += fo[q];
+            double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                j0 += cx(q) * fo[q];
+                j1 += cy(q) * fo[q];
+                j2 += cz(q) * fo[q];
+            }
+            double ux[3] = {j0 / rho_x - d.a[0], j1 / rho_x - d.a[1], j2 / rho_x - d.a[2]};
+            fp[0] = fo[0];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                int qb = opp(q);
+                if (scl[q] == CL_WALL || scl[q] == CL_O) {
+                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q) : 0.0;
+                    fp[q] = fo[qb] + ((6.0 * wd(q)) * rho_x) * cuw;
+                } else if (scl[q] == CL_G) {
+                    fp[q] = (feq_d(q, d.rho_g, ux) + feq_d(qb, d.rho_g, ux)) - fo[qb];
+                } else {
+                    fp[q] = P::ld(d.fsrc, q, src[q], N);
+                }
+            }
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
+                if (cn < -NORMAL_DEADBAND && scl[q] != CL_O && scl[q] != CL_WALL) {
+                    int qb = opp(q);
+                    fp[q] = (feq_d(q, d.rho_g, ux) + feq_d(qb, d.rho_g, ux)) - fo[qb];
+                }
+            }
+            double dm = 0.0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                int qb = opp(q);
+                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+                int yc = cls(d, yi);
+                if (yc == CL_L) {
+                    dm += P::ld(d.fsrc, qb, yi, N) - fo[q];
+                } else if (yc == CL_I) {
+                    double wgt = 0.5 * (own_phi + d.phisrc[yi]);
+                    dm += wgt * (P::ld(d.fsrc, qb, yi, N) - fo[q]);
+                }
+            }
+            m_new = d.m[i] + dm;
+            double fn[Q];
+            collide_d(d, fp, fn);
+            double r = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                P::st(d.fdst, q, i, N, fn[q]);
+                r += fn[q];
+            }
+            double phin = m_new / r;
+            d.m[i] = m_new;
+            d.phidst[i] = phin;
+            if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
+            uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+            if (mk) d.cmark[i] = mk;
+            wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
+            wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
+        } else {
+            float fo[Q], fp[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
+            float drx = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                drx += fo[q];
+                if (cx(q)) j0 += cx(q) * fo[q];
+                if (cy(q)) j1 += cy(q) * fo[q];
+                if (cz(q)) j2 += cz(q) * fo[q];
+            }
+            float rx = 1.0f + drx;
+            float ux = j0 / rx - (float)d.a[0], uy = j1 / rx - (float)d.a[1], uz = j2 / rx - (float)d.a[2];
+            float drg = (float)(d.rho_g - 1.0);
+            fp[0] = fo[0];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                int qb = opp(q);
+                if (scl[q] == CL_WALL || scl[q] == CL_O) {
+                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q) : 0.0;
+                    fp[q] = fo[qb] + (float)(6.0 * wd(q) * cuw) * rx;
+                } else if (scl[q] == CL_G) {
+                    fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
+                } else {
+                    fp[q] = P::ld(d.fsrc, q, src[q], N);
+                }
+            }
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
+                if (cn < -NORMAL_DEADBAND && scl[q] != CL_O && scl[q] != CL_WALL) {
+                    int qb = opp(q);
+                    fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
+                }
+            }
+            double dm = 0.0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                int qb = opp(q);
+                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+                int yc = cls(d, yi);
+                if (yc == CL_L) {
+                    dm += (double)(P::ld(d.fsrc, qb, yi, N) - fo[q]);
+                } else if (yc == CL_I) {
+                    double wgt = 0.5 * (own_phi + d.phisrc[yi]);
+                    dm += wgt * (double)(P::ld(d.fsrc, qb, yi, N) - fo[q]);
+                }
+            }
+            m_new = d.m[i] + dm;
+            float dn[Q], rho;
+            float dr = collide_f(d, fp, dn, rho);
+            P::st_dev(d.fdst, i, N, dn, dr);
+            double r = 0.0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) r += (double)P::ld(d.fdst, q, i, N);
+            r += 1.0;
+            double phin = m_new / r;
+            d.m[i] = m_new;
+            d.phidst[i] = phin;
+            if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+            uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+            if (mk) d.cmark[i] = mk;
+            wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
+            wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
+        }
+    }
+}
+
+// ------------------------------------------------- C3: conversions (Sec. 2.2)
+
+#define LIST_LOOP(L, var)                                                                                     \
+    uint32_t n_##var = wl_count(d, L);                                                                         \
+    for (uint32_t it_##var = blockIdx.x * blockDim.x + threadIdx.x; it_##var < n_##var;                        \
+         it_##var += gridDim.x * blockDim.x)
+
+// filled cells: emptied neighbours are kept; gas neighbours become interface
+__global__ void k_conv_filled(Dev d) {
+    LIST_LOOP(WL_FILLED, a) {
+        long long i = d.list[WL_FILLED][it_a];
+        int x, y, z;
+        coords(d, i, x, y, z);
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            if (yi < 0) continue;
+            if (d.cmark[yi] & MK_EMPTIED) mark_and(d, yi, MK_EMPTIED);
+            if (d.flags[yi] == CL_G) {
+                uint8_t old = mark_or(d, yi, MK_NEWG);
+                if (!(old & MK_NEWG)) {
+                    uint32_t pos = atomicAdd(&d.cnt[WL_NEWG], 1u);
+                    if (pos < d.cap) d.list[WL_NEWG][pos] = (uint32_t)yi;
+                    else atomicOr(d.status, ST_OVERFLOW);
+                }
+            }
+        }
+    }
+}
+
+// still-emptied cells: liquid neighbours become interface
+__global__ void k_conv_emptied(Dev d) {
+    LIST_LOOP(WL_EMPTIED, a) {
+        long long i = d.list[WL_EMPTIED][it_a];
+        if (!(d.cmark[i] & MK_EMPTIED)) continue;
+        int x, y, z;
+        coords(d, i, x, y, z);
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            if (yi < 0 || d.flags[yi] != CL_L) continue;
+            uint8_t old = mark_or(d, yi, MK_NEWL);
+            if (!(old & MK_NEWL)) {
+                uint32_t pos = atomicAdd(&d.cnt[WL_NEWL], 1u);
+                if (pos < d.cap) d.list[WL_NEWL][pos] = (uint32_t)yi;
+                else atomicOr(d.status, ST_OVERFLOW);
+            }
+        }
+    }
+}
+
+// new interface cells: from gas f = f_eq(mean rho, mean u) of the liquid and
+// interface neighbours, m = 0; from liquid m = rho
+template <int S>
+__global__ void k_conv_init(Dev d) {
+    {
+        LIST_LOOP(WL_NEWG, a) {
+            long long i = d.list[WL_NEWG][it_a];
+            int x, y, z;
+            coords(d, i, x, y, z);
+            double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
+            int cnt = 0;
+#pragma unroll 1
+            for (int q = 1; q < Q; ++q) {
+                long long zi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+                int zc = cls(d, zi);
+                if (zc != CL_L && zc != CL_I) continue;
+                double u[3];
+                double r = cell_rho_u<S>(d, d.fdst, zi, u);
+                sr += r;
+                su[0] += u[0];
+                su[1] += u[1];
+                su[2] += u[2];
+                cnt++;
+            }
+            double rm = sr / cnt;
+            double um[3] = {su[0] / cnt, su[1] / cnt, su[2] / cnt};
+            double f[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = feq_d(q, rm, um);
+            Sto<S>::st_cell(d.fdst, i, d.N, f);
+            d.m[i] = 0.0;
+        }
+    }
+    {
+        LIST_LOOP(WL_NEWL, b) {
+            long long i = d.list[WL_NEWL][it_b];
+            d.m[i] = cell_density<S>(d, d.fdst, i);
+        }
+    }
+}
+
+__global__ void k_conv_flags(Dev d) {
+    {
+        LIST_LOOP(WL_FILLED, a) d.flags[d.list[WL_FILLED][it_a]] = CL_L;
+    }
+    {
+        LIST_LOOP(WL_EMPTIED, b) {
+            long long i = d.list[WL_EMPTIED][it_b];
+            if (d.cmark[i] & MK_EMPTIED) d.flags[i] = CL_G;
+        }
+    }
+    {
+        LIST_LOOP(WL_NEWG, c) d.flags[d.list[WL_NEWG][it_c]] = CL_I;
+    }
+    {
+        LIST_LOOP(WL_NEWL, e) d.flags[d.list[WL_NEWL][it_e]] = CL_I;
+    }
+}
+
+// interface neighbours of converted cells receive excess mass
+__device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
+    int x, y, z;
+    coords(d, i, x, y, z);
+#pragma unroll 1
+    for (int q = 1; q < Q; ++q) {
+        long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+        if (yi < 0 || d.flags[yi] != CL_I) continue;
+        uint8_t old = mark_or(d, yi, MK_RECV);
+        if (!(old & MK_RECV)) {
+            uint32_t pos = atomicAdd(&d.cnt[WL_RECV], 1u);
+            if (pos < d.cap) d.list[WL_RECV][pos] = (uint32_t)yi;
+            else atomicOr(d.status, ST_OVERFLOW);
+        }
+    }
+}
+
+__global__ void k_conv_claim(Dev d) {
+    {
+        LIST_LOOP(WL_FILLED, a) claim_receivers(d, d.list[WL_FILLED][it_a]);
+    }
+    {
+        LIST_LOOP(WL_EMPTIED, b) {
+            long long i = d.list[WL_EMPTIED][it_b];
+            if (d.cmark[i] & MK_EMPTIED) claim_receivers(d, i);
+        }
+    }
+}
+
+// k(x): interface neighbours of a converted cell (classes after conversion)
+__device__ __forceinline__ int iface_neighbours(const Dev &d, long long i) {
+    int x, y, z;
+    coords(d, i, x, y, z);
+    int k = 0;
+#pragma unroll 1
+    for (int q = 1; q < Q; ++q) {
+        long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+        if (yi >= 0 && d.flags[yi] == CL_I) k++;
+    }
+    return k;
+}
+
+template <int S>
+__device__ __forceinline__ double excess(const Dev &d, long long i, uint8_t mk) {
+    return (mk & MK_FILLED) ? d.m[i] - cell_density<S>(d, d.fdst, i) : d.m[i];
+}
+
+// receivers gather e(x) / k(x) over their converted neighbours in q order
+template <int S>
+__global__ void k_conv_excess(Dev d) {
+    LIST_LOOP(WL_RECV, a) {
+        long long i = d.list[WL_RECV][it_a];
+        int x, y, z;
+        coords(d, i, x, y, z);
+        double acc = 0.0;
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            if (yi < 0) continue;
+            uint8_t mk = d.cmark[yi];
+            if (!(mk & (MK_FILLED | MK_EMPTIED))) continue;
+            acc += excess<S>(d, yi, mk) / iface_neighbours(d, yi);
+        }
+        double m = d.m[i] + acc;
+        d.m[i] = m;
+        d.phidst[i] = m / cell_density<S>(d, d.fdst, i);
+    }
+}
+
+// mass that found no interface neighbour goes to the ledger; marks are cleared
+template <int S>
+__global__ void k_conv_finish(Dev d) {
+    {
+        LIST_LOOP(WL_FILLED, a) {
+            long long i = d.list[WL_FILLED][it_a];
+            if (iface_neighbours(d, i) == 0) atomicAdd(&d.ledger[LG_LOST], excess<S>(d, i, MK_FILLED));
+            d.cmark[i] = 0;
+        }
+    }
+    {
+        LIST_LOOP(WL_EMPTIED, b) {
+            long long i = d.list[WL_EMPTIED][it_b];
+            uint8_t mk = d.cmark[i];
+            if ((mk & MK_EMPTIED) && iface_neighbours(d, i) == 0) atomicAdd(&d.ledger[LG_LOST], excess<S>(d, i, mk));
+            d.cmark[i] = 0;
+        }
+    }
+    {
+        LIST_LOOP(WL_NEWG, c) d.cmark[d.list[WL_NEWG][it_c]] = 0;
+    }
+    {
+        LIST_LOOP(WL_NEWL, e) d.cmark[d.list[WL_NEWL][it_e]] = 0;
+    }
+    {
+        LIST_LOOP(WL_RECV, g) d.cmark[d.list[WL_RECV][it_g]] = 0;
+    }
+}
+
+// ----------------------------------------------- C5: rigid-body update
+
+// one warp per body: fixed-order sum of the force partials, then the update
+__global__ void k_bodies(Dev d) {
+    int bi = blockIdx.x;
+    Body &b = d.bodies[bi];
+    int lane = threadIdx.x;
+    double acc[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double v = 0.0;
+        for (int k = lane; k < FORCE_BLOCKS; k += 32) v += d.part[((long long)bi * FORCE_BLOCKS + k) * 7 + c];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        acc[c] = v;
+    }
+    if (lane != 0) return;
+    for (int k = 0; k < 3; ++k) {
+        b.F[k] = acc[k];
+        b.T[k] = acc[3 + k];
+    }
+    b.S = acc[6];
+    for (int k = 0; k < 3; ++k) {
+        b.plo[k] = b.lo[k];
+        b.phi[k] = b.hi[k];
+    }
+    int base = b.mode & 0xff;
+    if (base == 0) {
+        for (int k = 0; k < 3; ++k) b.v[k] = b.w[k] = b.dv[k] = b.dw[k] = 0.0;
+        return;
+    }
+    double vol = ((8.0 * b.h[0]) * b.h[1]) * b.h[2];
+    double mass = b.dens * vol;
+    double I[3] = {(mass / 3.0) * (b.h[1] * b.h[1] + b.h[2] * b.h[2]), (mass / 3.0) * (b.h[0] * b.h[0] + b.h[2] * b.h[2]),
+                   (mass / 3.0) * (b.h[0] * b.h[0] + b.h[1] * b.h[1])};
+    double If[3] = {I[0] / b.dens, I[1] / b.dens, I[2] / b.dens};
+    double den = mass + VIRTUAL_MASS * vol;
+    for (int k = 0; k < 3; ++k) {
+        double num = (b.F[k] + mass * d.grav[k]) + VIRTUAL_MASS * (vol * b.dv[k]);
+        b.dv[k] = num / den;
+        b.v[k] = b.v[k] + b.dv[k];
+    }
+    if (b.mode & 0x100)
+        for (int k = 0; k < 3; ++k) b.v[k] = b.v[k] * (1.0 - b.damp);
+    double R[9];
+    rotation(b.q, R);
+    if (base == 2) {
+        const double *ax = b.axis;
+        double ta = (b.T[0] * ax[0] + b.T[1] * ax[1]) + b.T[2] * ax[2];
+        double ab[3];
+        for (int k = 0; k < 3; ++k) ab[k] = (R[0 * 3 + k] * ax[0] + R[1 * 3 + k] * ax[1]) + R[2 * 3 + k] * ax[2];
+        double Ia = (ab[0] * ab[0] * I[0] + ab[1] * ab[1] * I[1]) + ab[2] * ab[2] * I[2];
+        double Ifa = Ia / b.dens;
+        double ws = (b.w[0] * ax[0] + b.w[1] * ax[1]) + b.w[2] * ax[2];
+        b.dw[0] = (ta + VIRTUAL_MASS * (Ifa * b.dw[0])) / (Ia + VIRTUAL_MASS * Ifa);
+        ws = ws + b.dw[0];
+        for (int k = 0; k < 3; ++k) b.w[k] = ws * ax[k];
+    } else {
+        double wb[3], tb[3], L[3], gy[3];
+        for (int k = 0; k < 3; ++k) {
+            wb[k] = (R[0 * 3 + k] * b.w[0] + R[1 * 3 + k] * b.w[1]) + R[2 * 3 + k] * b.w[2];
+            tb[k] = (R[0 * 3 + k] * b.T[0] + R[1 * 3 + k] * b.T[1]) + R[2 * 3 + k] * b.T[2];
+            L[k] = I[k] * wb[k];
+        }
+        gy[0] = wb[1] * L[2] - wb[2] * L[1];
+        gy[1] = wb[2] * L[0] - wb[0] * L[2];
+        gy[2] = wb[0] * L[1] - wb[1] * L[0];
+        for (int k = 0; k < 3; ++k) {
+            b.dw[k] = ((tb[k] - gy[k]) + VIRTUAL_MASS * (If[k] * b.dw[k])) / (I[k] + VIRTUAL_MASS * If[k]);
+            wb[k] = wb[k] + b.dw[k];
+        }
+        for (int k = 0; k < 3; ++k) b.w[k] = (R[k * 3 + 0] * wb[0] + R[k * 3 + 1] * wb[1]) + R[k * 3 + 2] * wb[2];
+    }
+    double nn[3] = {(double)d.nx, (double)d.ny, (double)d.nz};
+    for (int k = 0; k < 3; ++k) {
+        b.o[k] = b.o[k] + b.v[k];
+        if (d.periodic & (1u << k)) {
+            if (b.o[k] >= nn[k]) b.o[k] = b.o[k] - nn[k];
+            else if (b.o[k] < 0.0) b.o[k] = b.o[k] + nn[k];
+        }
+    }
+    double qw = b.q[0], qx = b.q[1], qy = b.q[2], qz = b.q[3];
+    const double *w = b.w;
+    double dw = -((w[0] * qx + w[1] * qy) + w[2] * qz);
+    double dx = qw * w[0] + (w[1] * qz - w[2] * qy);
+    double dy = qw * w[1] + (w[2] * qx - w[0] * qz);
+    double dz = qw * w[2] + (w[0] * qy - w[1] * qx);
+    double nq[4] = {qw + 0.5 * dw, qx + 0.5 * dx, qy + 0.5 * dy, qz + 0.5 * dz};
+    double norm = sqrt(((nq[0] * nq[0] + nq[1] * nq[1]) + nq[2] * nq[2]) + nq[3] * nq[3]);
+    for (int k = 0; k < 4; ++k) b.q[k] = nq[k] / norm;
+    body_bounds(d, b);
+}
+
+// ----------------------------------------------- C6: remap (Sec. 2.3, 2.4)
+
+// cells inside body blockIdx.y at its new pose become obstacle
+template <int S>
+__global__ void k_remap_cover(Dev d) {
+    int bi = blockIdx.y;
+    const Body &b = d.bodies[bi];
+    long long n = range_count(b.lo, b.hi);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        range_cell(d, b.lo, b.hi, k, x, y, z);
+        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+        int c = d.flags[i];
+        if (c == CL_O || !inside(d, b, x, y, z)) continue;
+        double mass = c == CL_L ? cell_density<S>(d, d.fdst, i) : (c == CL_I ? d.m[i] : 0.0);
+        if (mass != 0.0) atomicAdd(&d.ledger[LG_COVERED], mass);
+        d.flags[i] = CL_O;
+        d.bid[i] = (uint8_t)bi;
+    }
+}
+
+// obstacle cells of body blockIdx.y outside its new pose are pending
+__global__ void k_remap_pending(Dev d) {
+    int bi = blockIdx.y;
+    const Body &b = d.bodies[bi];
+    long long n = range_count(b.plo, b.phi);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        range_cell(d, b.plo, b.phi, k, x, y, z);
+        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+        bool pend = d.flags[i] == CL_O && d.bid[i] == bi && !inside(d, b, x, y, z);
+        if (pend) d.cmark[i] = MK_PEND;
+        wl_append(d, pend, WL_PEND, (uint32_t)i);
+    }
+}
+
+// Jacobi passes of the obstacle-to-fluid rule over the pending cells, closure,
+// uncovered-mass ledger (one block)
+template <int S>
+__global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
+    uint32_t n = wl_count(d, WL_PEND);
+    if (n == 0) return;
+    __shared__ int s_any;
+    for (int pass = 0; pass < 4; ++pass) {
+        for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
+            long long i = d.list[WL_PEND][it];
+            d.rdec[it] = 0;
+            if (!(d.cmark[i] & MK_PEND)) continue;
+            int x, y, z;
+            coords(d, i, x, y, z);
+            int nL = 0, nI = 0, nG = 0;
+            double sr = 0.0, sp = 0.0;
+            for (int q = 1; q < Q; ++q) {
+                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+                if (yi < 0 || (d.cmark[yi] & MK_PEND) || d.flags[yi] == CL_O) continue;
+                int c = d.flags[yi];
+                if (c == CL_L) {
+                    nL++;
+                    sr += cell_density<S>(d, d.fdst, yi);
+                } else if (c == CL_I) {
+                    nI++;
+                    sr += cell_density<S>(d, d.fdst, yi);
+                    sp += d.phidst[yi];
+                } else if (c == CL_G) {
+                    nG++;
+                }
+            }
+            uint8_t dec = 0;
+            if (nL > 0 && nG > 0) {
+                dec = CL_I;
+                d.rrho[it] = sr / (nL + nI);
+                d.rphi[it] = nI > 0 ? sp / nI : 0.5;
+            } else if (nG == 0 && nL + nI > 0) {
+                dec = CL_L;
+                d.rrho[it] = sr / (nL + nI);
+            } else if (nL == 0 && nG > 0) {
+                dec = CL_G;
+            }
+            d.rdec[it] = dec;
+        }
+        if (threadIdx.x == 0) s_any = 0;
+        __syncthreads();
+        for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
+            long long i = d.list[WL_PEND][it];
+            if (!(d.cmark[i] & MK_PEND)) continue;
+            int dec = d.rdec[it];
+            if (dec == 0 && pass == 3) dec = CL_G;
+            if (dec == 0) {
+                s_any = 1;
+                continue;
+            }
+            const Body &b = d.bodies[d.bid[i]];
+            d.cmark[i] = MK_FRESH;
+            d.flags[i] = (uint8_t)dec;
+            if (dec == CL_G) continue;
+            int x, y, z;
+            coords(d, i, x, y, z);
+            double p[3] = {x + 0.5, y + 0.5, z + 0.5}, uw[3];
+            body_velocity_at(d, b, p, uw);
+            double f[Q];
+            double rho = d.rrho[it];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = feq_d(q, rho, uw);
+            Sto<S>::st_cell(d.fdst, i, d.N, f);
+            if (dec == CL_I) {
+                double m = d.rphi[it] * rho;
+                d.m[i] = m;
+                d.phidst[i] = m / cell_density<S>(d, d.fdst, i);
+            }
+        }
+        __syncthreads();
+        if (!s_any) break;
+        __syncthreads();
+    }
+    // closure: a new liquid cell next to gas becomes interface with phi = 1
+    for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
+        long long i = d.list[WL_PEND][it];
+        if (!(d.cmark[i] & MK_FRESH) || d.flags[i] != CL_L) continue;
+        int x, y, z;
+        coords(d, i, x, y, z);
+        bool gas = false;
+        for (int q = 1; q < Q; ++q) {
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            if (yi >= 0 && d.flags[yi] == CL_G) gas = true;
+        }
+        d.rdec[it] = gas ? 1 : 0;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
+        long long i = d.list[WL_PEND][it];
+        if (!(d.cmark[i] & MK_FRESH)) continue;
+        if (d.flags[i] == CL_L && d.rdec[it]) {
+            d.flags[i] = CL_I;
+            double r = cell_density<S>(d, d.fdst, i);
+            d.m[i] = r;
+            d.phidst[i] = d.m[i] / cell_density<S>(d, d.fdst, i);
+        }
+        if (d.flags[i] == CL_L) acc += cell_density<S>(d, d.fdst, i);
+        else if (d.flags[i] == CL_I) acc += d.m[i];
+        d.cmark[i] = 0;
+    }
+    __shared__ double sh[REMAP_THREADS / 32];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        d.ledger[LG_UNCOVERED] += t;
+    }
+}
+
+// ------------------------------------------------------ reductions, output
+
+// sum over liquid rho + interface m -> red[block]
+template <int S>
+__global__ void __launch_bounds__(256) k_mass_partial(Dev d) {
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)gridDim.x * blockDim.x) {
+        int c = d.flags[i];
+        if (c == CL_L) acc += cell_density<S>(d, d.fsrc, i);
+        else if (c == CL_I) acc += d.m[i];
+    }
+    __shared__ double sh[8];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        d.red[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_mass_final(Dev d, int nblk) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int k = 0; k < nblk; ++k) t += d.red[k];
+    d.ledger[LG_MASS] = t;
+}
+
+template <int S>
+__global__ void k_read_fields(Dev d, unsigned mask, uint8_t *flags, double *fill, double *mass, double *rho, double *vel,
+                              double *f) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    int c = d.flags[i];
+    bool fluid = c == CL_L || c == CL_I;
+    double u[3] = {0.0, 0.0, 0.0};
+    double r = fluid ? cell_rho_u<S>(d, d.fsrc, i, u) : 0.0;
+    if (flags) flags[i] = (uint8_t)c;
+    if (fill) fill[i] = c == CL_L ? 1.0 : (c == CL_I ? d.phisrc[i] : 0.0);
+    if (mass) mass[i] = c == CL_L ? r : (c == CL_I ? d.m[i] : 0.0);
+    if (rho) rho[i] = r;
+    if (vel) {
+        vel[3 * i] = u[0];
+        vel[3 * i + 1] = u[1];
+        vel[3 * i + 2] = u[2];
+    }
+    if (f)
+        for (int q = 0; q < Q; ++q) f[(long long)q * d.N + i] = fluid ? Sto<S>::ldf(d.fsrc, q, i, d.N) : 0.0;
+}
+
+// ------------------------------------------------------------ launchers
+
+template <int S> struct Launch {
+    static void init_cells(const Dev &d, const uint8_t *flags, const double *fill, const double *rho, const double *vel,
+                           cudaStream_t st) {
+        unsigned blocks = (unsigned)((d.N + 255) / 256);
+        k_init<S><<<blocks, 256, 0, st>>>(d, flags, fill, rho, vel);
+    }
+    static void body_prepare(const Dev &d, int b, cudaStream_t st) { k_body_prepare<<<1, 32, 0, st>>>(d, b); }
+    static void map_body(const Dev &d, int b, int book, cudaStream_t st) {
+        k_map_body<S><<<FORCE_BLOCKS, 256, 0, st>>>(d, b, book);
+    }
+    static void liquid_mass(const Dev &d, cudaStream_t st) {
+        k_mass_partial<S><<<LIST_BLOCKS, 256, 0, st>>>(d);
+        k_mass_final<<<1, 32, 0, st>>>(d, LIST_BLOCKS);
+    }
+    static void read_fields(const Dev &d, unsigned mask, void *const *dst, cudaStream_t st) {
+        unsigned blocks = (unsigned)((d.N + 255) / 256);
+        k_read_fields<S><<<blocks, 256, 0, st>>>(
+            d, mask, (mask & 1u) ? (uint8_t *)dst[0] : nullptr, (mask & 2u) ? (double *)dst[1] : nullptr,
+            (mask & 4u) ? (double *)dst[2] : nullptr, (mask & 8u) ? (double *)dst[3] : nullptr,
+            (mask & 16u) ? (double *)dst[4] : nullptr, (mask & 32u) ? (double *)dst[5] : nullptr);
+    }
+    // one time step; with ev != nullptr, event k is recorded before kernel k
+    // and ev[count] after the last one
+    static int step(const Dev &d, cudaStream_t st, float *, cudaEvent_t *ev) {
+        int k = 0;
+        auto mark = [&]() {
+            if (ev) cudaEventRecord(ev[k], st);
+            ++k;
+        };
+        mark();
+        cudaMemsetAsync(d.cnt, 0, WL_COUNT * sizeof(uint32_t), st);
+        mark();
+        if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
+        mark();
+        k_liquid<S><<<dim3((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, d.nz), BULK_THREADS, 0, st>>>(d);
+        mark();
+        k_interface<S><<<LIST_BLOCKS * 2, 128, 0, st>>>(d);
+        mark();
+        k_conv_filled<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_emptied<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_init<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_flags<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_claim<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_excess<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        k_conv_finish<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        if (d.nb > 0) k_bodies<<<d.nb, 32, 0, st>>>(d);
+        mark();
+        if (d.nb > 0) k_remap_cover<S><<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
+        mark();
+        if (d.nb > 0) k_remap_pending<<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
+        mark();
+        if (d.nb > 0) k_remap_resolve<S><<<1, REMAP_THREADS, 0, st>>>(d);
+        mark();
+        return d.nb > 0 ? 14 : 9;  // kernels (the counter reset is a memset node)
+    }
+};
+
+inline const char *const *kernel_names() {
+    static const char *const n[] = {"reset_counters", "forces", "liquid", "interface", "conv_filled",
+                                    "conv_emptied",    "conv_init", "conv_flags", "conv_claim", "conv_excess",
+                                    "conv_finish",     "bodies",  "remap_cover", "remap_pending", "remap_resolve"};
+    return n;
+}
+
+template <int S> KernelSet make_kernel_set() {
+    KernelSet k;
+    k.init_cells = &Launch<S>::init_cells;
+    k.body_prepare = &Launch<S>::body_prepare;
+    k.map_body = &Launch<S>::map_body;
+    k.step = &Launch<S>::step;
+    k.liquid_mass = &Launch<S>::liquid_mass;
+    k.read_fields = &Launch<S>::read_fields;
+    k.nkernels = 15;
+    k.names = kernel_names();
+    return k;
+}
+
+}  // namespace
+}  // namespace lbmfs

