@@ -560,6 +560,23 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
     }
 }
 
+// Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
+// an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
+// Kept out of line so that the bulk kernel's populations stay in registers.
+template <int S>
+__device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long long si, int ns, long long i, int x,
+                                                       int y, int z) {
+    using R = typename Sto<S>::R;
+    int qb = opp(q);
+    R own = Sto<S>::ld(d.fsrc, qb, i, d.N);
+    double cuw = 0.0;
+    if (ns == CL_O) cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
+    else if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
+    if (cuw == 0.0) return own;
+    double rho_x = cell_density<S>(d, d.fsrc, i);
+    return (R)((double)own + ((6.0 * wd(q)) * rho_x) * cuw);
+}
+
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
 template <int S>
 __global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
@@ -576,40 +593,14 @@ __global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
     const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
     R fp[Q];
-    unsigned special = 0;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long si = interior ? i - (cx(q) * sx + cy(q) * sy + cz(q) * sz) : nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
         int ns = si < 0 ? CL_WALL : (int)d.flags[si];
         if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
-        else special |= 1u << q;
+        else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
     }
     fp[0] = P::ld(d.fsrc, 0, i, N);
-    if (special) {
-        // Eq. noslip at walls and obstacles: f'_q = f*_qbar + 6 w_q rho (c_q.u_w)
-        bool have_rho = false;
-        double rho_x = 0.0;
-#pragma unroll 1
-        for (int q = 1; q < Q; ++q) {
-            if (!(special & (1u << q))) continue;
-            int qb = opp(q);
-            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            int ns = cls(d, si);
-            double cuw = 0.0;
-            if (ns == CL_O) cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
-            else if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
-            R own = P::ld(d.fsrc, qb, i, N);
-            if (cuw == 0.0) {
-                fp[q] = own;
-            } else {
-                if (!have_rho) {
-                    rho_x = cell_density<S>(d, d.fsrc, i);
-                    have_rho = true;
-                }
-                fp[q] = (R)((double)own + ((6.0 * wd(q)) * rho_x) * cuw);
-            }
-        }
-    }
     if constexpr (!P::shifted) {
         double fn[Q];
         collide_d(d, fp, fn);

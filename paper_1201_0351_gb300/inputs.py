@@ -332,8 +332,17 @@ def random_box_scene(nx, ny, nz, seed: int, nboxes: int = 1, periodic: int = 0, 
     flags, fill, rho = hydrostatic_tank(nx, ny, nz, eta, g, 1.0, periodic)
     boxes = []
     for _ in range(nboxes):
-        half = (1.5 + 2.0 * rng.uniform(), 1.5 + 2.0 * rng.uniform(), 1.2 + 1.5 * rng.uniform())
-        c = (nx * (0.3 + 0.4 * rng.uniform()), ny * (0.3 + 0.4 * rng.uniform()), e0 + 2.0 * (rng.uniform() - 0.5))
+        # bodies must not touch each other or the walls (contacts are not modelled)
+        for _try in range(1000):
+            half = (1.5 + 2.0 * rng.uniform(), 1.5 + 2.0 * rng.uniform(), 1.2 + 1.5 * rng.uniform())
+            c = (nx * (0.2 + 0.6 * rng.uniform()), ny * (0.2 + 0.6 * rng.uniform()), e0 + 2.0 * (rng.uniform() - 0.5))
+            r = math.sqrt(sum(h * h for h in half))
+            ok = all(r + 2.0 < c[k] < n - r - 2.0 for k, n in enumerate((nx, ny, nz)))
+            ok = ok and all(math.dist(c, b.center) > r + math.sqrt(sum(h * h for h in b.half)) + 2.0 for b in boxes)
+            if ok:
+                break
+        else:
+            raise ValueError("no room for %d boxes in %dx%dx%d" % (nboxes, nx, ny, nz))
         ax = (rng.uniform() - 0.5, rng.uniform() - 0.5, rng.uniform() - 0.5)
         nrm = math.sqrt(sum(a * a for a in ax)) or 1.0
         ang = 40.0 * rng.uniform()
