@@ -126,6 +126,10 @@ typedef struct {
     int64_t n_interface, n_filled, n_emptied, n_new_from_gas, n_new_from_liquid, n_pending;
     uint32_t status;       /* sticky device status bits */
     int64_t kernel_launches; /* kernels launched by this handle so far */
+    double wall_source;    /* mass added to liquid cells by the moving-wall term
+                              6 w_q rho (c_q . u_w) of Eq. noslip.  Ledger identity:
+                              liquid_mass = mass0 + uncovered - covered
+                              - lost_excess + wall_source (to rounding) */
 } lbm_fs_stats_t;
 
 /* field selectors for lbm_fs_read_fields / lbm_fs_write_fields; dst[k] is the

@@ -22,7 +22,7 @@
  * Eq. forceterm are garbled), the cell's own density in the moving-wall term,
  * u_w at the link midpoint, the anti-bounce-back of the cell's own outgoing
  * population in Eq. reconstruct, a central-difference normal with
- * c.n < -1e-6 (a dead band against rounding noise), eps = 1e-2, Jacobi-style conversions with equal excess-mass split,
+ * c.n < -1e-3 (a dead band against noise), eps = 1e-2, Jacobi-style conversions with equal excess-mass split,
  * and the obstacle-to-fluid priority interface > liquid > gas.
  *
  * Floating-point expression order is written out explicitly (left to right,
@@ -40,10 +40,12 @@
 enum { LIQ = 1, IFC = 2, GAS = 4, OBS = 8, WALL = 256 };
 enum { M_FIXED = 0, M_FREE = 1, M_ROT_AXIS = 2, M_DAMP = 0x100 };
 /* Eq. reconstruct selects the directions with c_q . n <= 0.  A direction
- * tangential to a flat surface has c_q . n = 0 up to rounding noise, and a
- * bare sign test would turn that noise into a reconstruct / stream decision;
- * directions count as pointing out of the gas only when c_q . n < -1e-6. */
-#define NORMAL_DEADBAND 1e-6
+ * tangential to a flat surface has c_q . n = 0 up to noise (rounding, storage
+ * precision), and a bare sign test turns that noise into a discontinuous
+ * reconstruct / stream decision; directions count as pointing out of the gas
+ * only when c_q . n < -1e-3, i.e. when the fill level changes by more than
+ * 2e-3 across the cell. */
+#define NORMAL_DEADBAND 1e-3
 
 /* D3Q19 velocities in the order of the paper's stencil figure. */
 static const int C[Q][3] = {
@@ -93,6 +95,7 @@ struct orc_sim {
     int nb, cap;
     body_t *b;
     double covered, uncovered, lost, M0;
+    double wall; /* mass added to liquid cells by the moving-wall term of Eq. noslip */
     int have_m0, err;
     long t;
     long counts[6];
@@ -405,7 +408,9 @@ static void stream_collide(orc_sim *s) {
                         double uw[3] = {0.0, 0.0, 0.0};
                         if (scl[q] == OBS) link_wall_velocity(s, &s->b[s->body[src[q]]], x, y, z, q, uw);
                         double cuw = (C[q][0] * uw[0] + C[q][1] * uw[1]) + C[q][2] * uw[2];
-                        fp[q] = (g_mutation == 6 ? fo[q] : fo[qb]) + ((6.0 * W[q]) * rho_x) * cuw;
+                        double src_term = ((6.0 * W[q]) * rho_x) * cuw;
+                        fp[q] = (g_mutation == 6 ? fo[q] : fo[qb]) + src_term;
+                        if (cl == LIQ) s->wall += src_term;
                     } else if (scl[q] == GAS) {
                         if (cl == LIQ) {
                             s->err |= ORC_ERR_LIQUID_GAS_ADJ;
@@ -874,6 +879,7 @@ void orc_get_ledger(const orc_sim *s, double out[5]) {
     out[2] = s->lost;
     out[3] = s->have_m0 ? s->M0 : liquid_mass(s);
     out[4] = liquid_mass(s);
+    out[5] = s->wall;
 }
 
 int orc_error(const orc_sim *s) { return s->err; }

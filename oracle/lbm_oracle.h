@@ -54,8 +54,9 @@ void orc_get_fields(const orc_sim *s, uint8_t *flags, double *fill, double *mass
 void orc_get_body(const orc_sim *s, int b, double F[3], double T[3], double *S,
                   double center[3], double quat[4], double vel[3], double omega[3]);
 /* ledger: [0] covered, [1] uncovered, [2] lost excess, [3] M at the first step,
- * [4] current liquid mass */
-void orc_get_ledger(const orc_sim *s, double out[5]);
+ * [4] current liquid mass, [5] mass added to liquid cells by the moving-wall
+ * term of Eq. noslip.  M = M0 + uncovered - covered - lost + wall. */
+void orc_get_ledger(const orc_sim *s, double out[6]);
 int orc_error(const orc_sim *s);
 long orc_time(const orc_sim *s);
 /* cells that the free-surface conversion handled in the last step */

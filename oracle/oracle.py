@@ -164,9 +164,9 @@ class OracleSim:
         return dict(F=F, T=T, S=S.value, center=c, quat=q, vel=v, omega=w)
 
     def ledger(self):
-        out = np.zeros(5)
+        out = np.zeros(6)
         self.lib.orc_get_ledger(self.h, _dp(out))
-        return dict(covered=out[0], uncovered=out[1], lost=out[2], M0=out[3], M=out[4])
+        return dict(covered=out[0], uncovered=out[1], lost=out[2], M0=out[3], M=out[4], wall=out[5])
 
     def counts(self):
         out = (C.c_long * 6)()

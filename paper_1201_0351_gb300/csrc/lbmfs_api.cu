@@ -449,6 +449,7 @@ lbm_fs_status lbm_fs_stats(lbm_fs *h, lbm_fs_stats_t *out) {
     out->n_pending = cnt[WL_PEND];
     out->status = status;
     out->kernel_launches = h->launches;
+    out->wall_source = lg[LG_WALL];
     return read_status(h);
 }
 

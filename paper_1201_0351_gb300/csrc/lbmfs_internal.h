@@ -26,7 +26,7 @@ enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
 // worklists
 enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COUNT };
 // ledger slots (double)
-enum { LG_COVERED = 0, LG_UNCOVERED, LG_LOST, LG_MASS0, LG_MASS, LG_COUNT };
+enum { LG_COVERED = 0, LG_UNCOVERED, LG_LOST, LG_MASS0, LG_MASS, LG_WALL, LG_COUNT };
 
 struct Body {
     double o[3], h[3], q[4], dens, v[3], w[3], axis[3], damp;

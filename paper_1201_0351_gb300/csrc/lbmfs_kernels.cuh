@@ -59,7 +59,9 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
     return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
 
-constexpr double NORMAL_DEADBAND = 1e-6;  // Eq. reconstruct: c.n < -1e-6
+// Eq. reconstruct selects c_q . n <= 0; tangential directions of a flat
+// surface sit at c.n = 0 up to noise, so only c.n < -1e-3 counts
+constexpr double NORMAL_DEADBAND = 1e-3;
 constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2015
 constexpr float F16_SCALE = 1024.0f;
 constexpr float F16_INV_SCALE = 1.0f / 1024.0f;
@@ -574,7 +576,9 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
     else if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
     if (cuw == 0.0) return own;
     double rho_x = cell_density<S>(d, d.fsrc, i);
-    return (R)((double)own + ((6.0 * wd(q)) * rho_x) * cuw);
+    double src = ((6.0 * wd(q)) * rho_x) * cuw;  // mass the moving wall adds to the liquid cell
+    atomicAdd(&d.ledger[LG_WALL], src);
+    return (R)((double)own + src);
 }
 
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
@@ -593,14 +597,32 @@ __global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
     const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
     R fp[Q];
+    if (interior) {
+        // every source lies inside the grid: issue the 18 flag loads and the 19
+        // population loads together (one memory round trip), fix up the rare
+        // obstacle links afterwards
+        int nf[Q];
 #pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        long long si = interior ? i - (cx(q) * sx + cy(q) * sy + cz(q) * sz) : nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-        int ns = si < 0 ? CL_WALL : (int)d.flags[si];
-        if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
-        else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
+        for (int q = 1; q < Q; ++q) {
+            long long si = i - (cx(q) * sx + cy(q) * sy + cz(q) * sz);
+            nf[q] = d.flags[si];
+            fp[q] = P::ld(d.fsrc, q, si, N);
+        }
+        fp[0] = P::ld(d.fsrc, 0, i, N);
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if (!(nf[q] & (CL_L | CL_I)))
+                fp[q] = bounce_back<S>(d, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), nf[q], i, x, y, z);
+    } else {
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            int ns = si < 0 ? CL_WALL : (int)d.flags[si];
+            if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
+            else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
+        }
+        fp[0] = P::ld(d.fsrc, 0, i, N);
     }
-    fp[0] = P::ld(d.fsrc, 0, i, N);
     if constexpr (!P::shifted) {
         double fn[Q];
         collide_d(d, fp, fn);

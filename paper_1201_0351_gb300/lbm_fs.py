@@ -53,7 +53,7 @@ class lbm_fs_stats_t(C.Structure):
                 ("uncovered", C.c_double), ("lost_excess", C.c_double), ("n_interface", C.c_int64),
                 ("n_filled", C.c_int64), ("n_emptied", C.c_int64), ("n_new_from_gas", C.c_int64),
                 ("n_new_from_liquid", C.c_int64), ("n_pending", C.c_int64), ("status", C.c_uint32),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("wall_source", C.c_double)]
 
 
 EXPORTS = ("lbm_fs_create", "lbm_fs_destroy", "lbm_fs_add_box", "lbm_fs_step", "lbm_fs_forces", "lbm_fs_body_state",

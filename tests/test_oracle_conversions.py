@@ -38,7 +38,7 @@ def _sim(n, flags, fill, rho, boxes=()):
 
 def _ledger_ok(s):
     L = s.ledger()
-    return abs(L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"])) <= 1e-12 * L["M0"]
+    return abs(L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"] + L["wall"])) <= 1e-12 * L["M0"]
 
 
 def test_filled_cell_converts_and_gas_neighbours_join_interface():

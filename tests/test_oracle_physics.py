@@ -104,7 +104,7 @@ def test_closed_tank_mass_conservation():
     s = oracle.OracleSim(sc)
     s.step(200)
     L = s.ledger()
-    resid = L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"])
+    resid = L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"] + L["wall"])
     assert abs(resid) <= 1e-13 * L["M0"]
     assert s.error == 0
 
@@ -155,7 +155,7 @@ def test_mass_mutation_is_caught():
     s = oracle.OracleSim(I.closed_tank_32())
     s.step(20)
     L = s.ledger()
-    assert abs(L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"])) > 1e-9 * L["M0"]
+    assert abs(L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"] + L["wall"])) > 1e-9 * L["M0"]
 
 
 # ---------------------------------------------------- Sec. 2.3 and 2.4
@@ -399,4 +399,18 @@ def test_galilean_body_follows_uniform_flow():
     f = s.fields()
     fluid = f["flags"] == I.LIQUID
     assert np.abs(f["u"][fluid] - u0).max() < 1e-12
+    assert s.error == 0
+
+
+def test_mass_ledger_with_moving_free_boxes():
+    """Liquid mass changes only through covered / uncovered cells, excess mass
+    that finds no interface neighbour, and the moving-wall term of Eq. noslip
+    (which adds 6 w rho c.u_w to a liquid cell at a moving obstacle link)."""
+    sc = I.random_box_scene(40, 30, 22, seed=5, nboxes=3, speed=0.02)
+    s = oracle.OracleSim(sc)
+    s.step(80)
+    L = s.ledger()
+    assert L["covered"] > 1 and L["uncovered"] > 1 and abs(L["wall"]) > 1e-3
+    resid = L["M"] - L["M0"] - (L["uncovered"] - L["covered"] - L["lost"] + L["wall"])
+    assert abs(resid) <= 1e-12 * L["M0"]
     assert s.error == 0
