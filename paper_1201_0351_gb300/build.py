@@ -47,16 +47,18 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile the library if any source is newer than it; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+    """Compile the library if any source is newer than it; returns its path.
+    extra_flags / out_dir build a variant elsewhere (tuning experiments)."""
+    lib = os.path.join(out_dir, os.path.basename(LIB))
+    if not force and out_dir == OUT_DIR and not extra_flags and up_to_date():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     nv = nvcc()
     objs = []
     cmds = []
     for unit, flags in UNITS.items():
-        obj = os.path.join(OUT_DIR, unit.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, unit.replace(".cu", ".o"))
         objs.append(obj)
         cmds.append([nv, *ARCH, *COMMON, *flags, *extra_flags, "-c", os.path.join(CSRC, unit), "-o", obj])
 
@@ -70,10 +72,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for out in ex.map(run, cmds):
             if verbose and out.strip():
                 print(out)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     run([nv, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

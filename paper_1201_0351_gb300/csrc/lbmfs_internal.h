@@ -12,10 +12,14 @@ constexpr int FORCE_BLOCKS = 64;   // blocks per body in the force / remap kerne
 constexpr int LIST_BLOCKS = 304;   // 2 x 152 SMs: grid of the worklist kernels
 constexpr int LIST_THREADS = 256;
 constexpr int REMAP_THREADS = 512;
-constexpr int BULK_THREADS = 128;  // x extent of a bulk-kernel block
+#ifndef LBMFS_BULK_THREADS
+#define LBMFS_BULK_THREADS 128
+#endif
+constexpr int BULK_THREADS = LBMFS_BULK_THREADS;  // x extent of a bulk-kernel block
 
-// cell classes (as in the C ABI)
-enum : uint8_t { CL_L = 1, CL_I = 2, CL_G = 4, CL_O = 8 };
+// cell classes (as in the C ABI) in the low nibble of the flag byte; bit 4
+// marks a cell with an obstacle or a wall among its 18 neighbours
+enum : uint8_t { CL_L = 1, CL_I = 2, CL_G = 4, CL_O = 8, CL_MASK = 15, NB_OBST = 16 };
 // per-cell conversion marks (separate byte array, zero between steps)
 enum : uint8_t {
     MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_PEND = 32, MK_FRESH = 64
@@ -24,7 +28,7 @@ enum : uint8_t {
 enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
 
 // worklists
-enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COUNT };
+enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_COUNT };
 // ledger slots (double)
 enum { LG_COVERED = 0, LG_UNCOVERED, LG_LOST, LG_MASS0, LG_MASS, LG_WALL, LG_COUNT };
 

@@ -63,6 +63,9 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 // surface sit at c.n = 0 up to noise, so only c.n < -1e-3 counts
 constexpr double NORMAL_DEADBAND = 1e-3;
 constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2015
+#ifndef LBMFS_BULK_MINB
+#define LBMFS_BULK_MINB 1  // minimum resident blocks per SM asked of ptxas for the bulk kernel
+#endif
 constexpr float F16_SCALE = 1024.0f;
 constexpr float F16_INV_SCALE = 1.0f / 1024.0f;
 constexpr int CL_WALL = 256;
@@ -182,7 +185,13 @@ __device__ __forceinline__ void coords(const Dev &d, long long idx, int &x, int 
     z = (int)(r / d.ny);
 }
 
-__device__ __forceinline__ int cls(const Dev &d, long long i) { return i < 0 ? CL_WALL : (int)d.flags[i]; }
+// class of cell i (the flag byte without the neighbour-obstacle bit); walls
+// (i < 0) report CL_WALL
+__device__ __forceinline__ int clsv(const Dev &d, long long i) { return (int)(d.flags[i] & CL_MASK); }
+__device__ __forceinline__ int cls(const Dev &d, long long i) { return i < 0 ? CL_WALL : clsv(d, i); }
+__device__ __forceinline__ void set_cls(const Dev &d, long long i, int c) {
+    d.flags[i] = (uint8_t)((d.flags[i] & NB_OBST) | c);
+}
 
 // warp-aggregated append of val to a worklist
 __device__ __forceinline__ void wl_append(const Dev &d, bool pred, int list, uint32_t val) {
@@ -470,14 +479,60 @@ __global__ void k_map_body(Dev d, int bi, int book_mass) {
         int x, y, z;
         range_cell(d, b.lo, b.hi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-        int c = d.flags[i];
+        int c = clsv(d, i);
         if (c == CL_O || !inside(d, b, x, y, z)) continue;
         if (book_mass) {
             double mass = c == CL_L ? cell_density<S>(d, d.fsrc, i) : (c == CL_I ? d.m[i] : 0.0);
             if (mass != 0.0) atomicAdd(&d.ledger[LG_COVERED], mass);
         }
-        d.flags[i] = CL_O;
+        set_cls(d, i, CL_O);
         d.bid[i] = (uint8_t)bi;
+    }
+}
+
+#define LIST_LOOP(L, var)                                                                                     \
+    uint32_t n_##var = wl_count(d, L);                                                                         \
+    for (uint32_t it_##var = blockIdx.x * blockDim.x + threadIdx.x; it_##var < n_##var;                        \
+         it_##var += gridDim.x * blockDim.x)
+
+// neighbour-obstacle bit: set when any of the 18 neighbours is an obstacle or
+// lies beyond a wall face (the bulk kernel then takes its general path)
+__device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
+    int x, y, z;
+    coords(d, i, x, y, z);
+    bool nb = false;
+#pragma unroll 1
+    for (int q = 1; q < Q; ++q) {
+        int c = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
+        nb = nb || c == CL_O || c == CL_WALL;
+    }
+    d.flags[i] = (uint8_t)((d.flags[i] & CL_MASK) | (nb ? NB_OBST : 0));
+}
+
+__global__ void k_nb_all(Dev d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)gridDim.x * blockDim.x)
+        nb_refresh(d, i);
+}
+
+// cells whose obstacle status changed this step (covered, uncovered): refresh
+// the bit of each and of its 18 neighbours
+__device__ __forceinline__ void nb_refresh_around(const Dev &d, long long i) {
+    int x, y, z;
+    coords(d, i, x, y, z);
+    nb_refresh(d, i);
+#pragma unroll 1
+    for (int q = 1; q < Q; ++q) {
+        long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+        if (yi >= 0) nb_refresh(d, yi);
+    }
+}
+
+__global__ void k_nb_update(Dev d) {
+    {
+        LIST_LOOP(WL_COVER, a) nb_refresh_around(d, d.list[WL_COVER][it_a]);
+    }
+    {
+        LIST_LOOP(WL_PEND, b) nb_refresh_around(d, d.list[WL_PEND][it_b]);
     }
 }
 
@@ -503,7 +558,7 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
         int x, y, z;
         range_cell(d, lo, hi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-        int cl = d.flags[i];
+        int cl = clsv(d, i);
         if (cl == CL_O) continue;
         double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
         bool have_rho = false;
@@ -513,7 +568,7 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
 #pragma unroll 1
         for (int q = 1; q < Q; ++q) {
             long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            if (si < 0 || d.flags[si] != CL_O || d.bid[si] != bi) continue;
+            if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
             double cuw = link_cuw(d, b, x, y, z, q);
             int qb = opp(q);
             double inner;
@@ -583,7 +638,7 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
 
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
+__global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid(Dev d) {
     using P = Sto<S>;
     using R = typename P::R;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -591,33 +646,23 @@ __global__ void __launch_bounds__(BULK_THREADS) k_liquid(Dev d) {
     bool in = x < d.nx;
     long long i = (long long)(in ? x : 0) + (long long)d.nx * (y + (long long)d.ny * z);
     int c = in ? (int)d.flags[i] : 0;
-    wl_append(d, c == CL_I, WL_IFACE, (uint32_t)i);
-    if (c != CL_L) return;
+    wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
+    if ((c & CL_MASK) != CL_L) return;
     const long long N = d.N;
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
     const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
     R fp[Q];
-    if (interior) {
-        // every source lies inside the grid: issue the 18 flag loads and the 19
-        // population loads together (one memory round trip), fix up the rare
-        // obstacle links afterwards
-        int nf[Q];
+    if (c == CL_L && interior) {
+        // no obstacle or wall in the neighbourhood and a liquid cell never
+        // touches gas: plain pull from the 18 neighbours, no flag loads
 #pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            long long si = i - (cx(q) * sx + cy(q) * sy + cz(q) * sz);
-            nf[q] = d.flags[si];
-            fp[q] = P::ld(d.fsrc, q, si, N);
-        }
+        for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
         fp[0] = P::ld(d.fsrc, 0, i, N);
-#pragma unroll
-        for (int q = 1; q < Q; ++q)
-            if (!(nf[q] & (CL_L | CL_I)))
-                fp[q] = bounce_back<S>(d, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), nf[q], i, x, y, z);
     } else {
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
             long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            int ns = si < 0 ? CL_WALL : (int)d.flags[si];
+            int ns = cls(d, si);
             if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
             else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
         }
@@ -819,11 +864,6 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
 
 // ------------------------------------------------- C3: conversions (Sec. 2.2)
 
-#define LIST_LOOP(L, var)                                                                                     \
-    uint32_t n_##var = wl_count(d, L);                                                                         \
-    for (uint32_t it_##var = blockIdx.x * blockDim.x + threadIdx.x; it_##var < n_##var;                        \
-         it_##var += gridDim.x * blockDim.x)
-
 // filled cells: emptied neighbours are kept; gas neighbours become interface
 __global__ void k_conv_filled(Dev d) {
     LIST_LOOP(WL_FILLED, a) {
@@ -835,7 +875,7 @@ __global__ void k_conv_filled(Dev d) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
             if (yi < 0) continue;
             if (d.cmark[yi] & MK_EMPTIED) mark_and(d, yi, MK_EMPTIED);
-            if (d.flags[yi] == CL_G) {
+            if (clsv(d, yi) == CL_G) {
                 uint8_t old = mark_or(d, yi, MK_NEWG);
                 if (!(old & MK_NEWG)) {
                     uint32_t pos = atomicAdd(&d.cnt[WL_NEWG], 1u);
@@ -857,7 +897,7 @@ __global__ void k_conv_emptied(Dev d) {
 #pragma unroll 1
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            if (yi < 0 || d.flags[yi] != CL_L) continue;
+            if (yi < 0 || clsv(d, yi) != CL_L) continue;
             uint8_t old = mark_or(d, yi, MK_NEWL);
             if (!(old & MK_NEWL)) {
                 uint32_t pos = atomicAdd(&d.cnt[WL_NEWL], 1u);
@@ -911,19 +951,19 @@ __global__ void k_conv_init(Dev d) {
 
 __global__ void k_conv_flags(Dev d) {
     {
-        LIST_LOOP(WL_FILLED, a) d.flags[d.list[WL_FILLED][it_a]] = CL_L;
+        LIST_LOOP(WL_FILLED, a) set_cls(d, d.list[WL_FILLED][it_a], CL_L);
     }
     {
         LIST_LOOP(WL_EMPTIED, b) {
             long long i = d.list[WL_EMPTIED][it_b];
-            if (d.cmark[i] & MK_EMPTIED) d.flags[i] = CL_G;
+            if (d.cmark[i] & MK_EMPTIED) set_cls(d, i, CL_G);
         }
     }
     {
-        LIST_LOOP(WL_NEWG, c) d.flags[d.list[WL_NEWG][it_c]] = CL_I;
+        LIST_LOOP(WL_NEWG, c) set_cls(d, d.list[WL_NEWG][it_c], CL_I);
     }
     {
-        LIST_LOOP(WL_NEWL, e) d.flags[d.list[WL_NEWL][it_e]] = CL_I;
+        LIST_LOOP(WL_NEWL, e) set_cls(d, d.list[WL_NEWL][it_e], CL_I);
     }
 }
 
@@ -934,7 +974,7 @@ __device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
 #pragma unroll 1
     for (int q = 1; q < Q; ++q) {
         long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-        if (yi < 0 || d.flags[yi] != CL_I) continue;
+        if (yi < 0 || clsv(d, yi) != CL_I) continue;
         uint8_t old = mark_or(d, yi, MK_RECV);
         if (!(old & MK_RECV)) {
             uint32_t pos = atomicAdd(&d.cnt[WL_RECV], 1u);
@@ -964,7 +1004,7 @@ __device__ __forceinline__ int iface_neighbours(const Dev &d, long long i) {
 #pragma unroll 1
     for (int q = 1; q < Q; ++q) {
         long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-        if (yi >= 0 && d.flags[yi] == CL_I) k++;
+        if (yi >= 0 && clsv(d, yi) == CL_I) k++;
     }
     return k;
 }
@@ -1129,11 +1169,13 @@ __global__ void k_remap_cover(Dev d) {
         int x, y, z;
         range_cell(d, b.lo, b.hi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-        int c = d.flags[i];
-        if (c == CL_O || !inside(d, b, x, y, z)) continue;
+        int c = clsv(d, i);
+        bool cover = c != CL_O && inside(d, b, x, y, z);
+        wl_append(d, cover, WL_COVER, (uint32_t)i);
+        if (!cover) continue;
         double mass = c == CL_L ? cell_density<S>(d, d.fdst, i) : (c == CL_I ? d.m[i] : 0.0);
         if (mass != 0.0) atomicAdd(&d.ledger[LG_COVERED], mass);
-        d.flags[i] = CL_O;
+        set_cls(d, i, CL_O);
         d.bid[i] = (uint8_t)bi;
     }
 }
@@ -1147,7 +1189,7 @@ __global__ void k_remap_pending(Dev d) {
         int x, y, z;
         range_cell(d, b.plo, b.phi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-        bool pend = d.flags[i] == CL_O && d.bid[i] == bi && !inside(d, b, x, y, z);
+        bool pend = clsv(d, i) == CL_O && d.bid[i] == bi && !inside(d, b, x, y, z);
         if (pend) d.cmark[i] = MK_PEND;
         wl_append(d, pend, WL_PEND, (uint32_t)i);
     }
@@ -1171,8 +1213,8 @@ __global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
             double sr = 0.0, sp = 0.0;
             for (int q = 1; q < Q; ++q) {
                 long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                if (yi < 0 || (d.cmark[yi] & MK_PEND) || d.flags[yi] == CL_O) continue;
-                int c = d.flags[yi];
+                if (yi < 0 || (d.cmark[yi] & MK_PEND) || clsv(d, yi) == CL_O) continue;
+                int c = clsv(d, yi);
                 if (c == CL_L) {
                     nL++;
                     sr += cell_density<S>(d, d.fdst, yi);
@@ -1210,7 +1252,7 @@ __global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
             }
             const Body &b = d.bodies[d.bid[i]];
             d.cmark[i] = MK_FRESH;
-            d.flags[i] = (uint8_t)dec;
+            set_cls(d, i, dec);
             if (dec == CL_G) continue;
             int x, y, z;
             coords(d, i, x, y, z);
@@ -1234,13 +1276,13 @@ __global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
     // closure: a new liquid cell next to gas becomes interface with phi = 1
     for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
         long long i = d.list[WL_PEND][it];
-        if (!(d.cmark[i] & MK_FRESH) || d.flags[i] != CL_L) continue;
+        if (!(d.cmark[i] & MK_FRESH) || clsv(d, i) != CL_L) continue;
         int x, y, z;
         coords(d, i, x, y, z);
         bool gas = false;
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            if (yi >= 0 && d.flags[yi] == CL_G) gas = true;
+            if (yi >= 0 && clsv(d, yi) == CL_G) gas = true;
         }
         d.rdec[it] = gas ? 1 : 0;
     }
@@ -1249,14 +1291,14 @@ __global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
     for (uint32_t it = threadIdx.x; it < n; it += blockDim.x) {
         long long i = d.list[WL_PEND][it];
         if (!(d.cmark[i] & MK_FRESH)) continue;
-        if (d.flags[i] == CL_L && d.rdec[it]) {
-            d.flags[i] = CL_I;
+        if (clsv(d, i) == CL_L && d.rdec[it]) {
+            set_cls(d, i, CL_I);
             double r = cell_density<S>(d, d.fdst, i);
             d.m[i] = r;
             d.phidst[i] = d.m[i] / cell_density<S>(d, d.fdst, i);
         }
-        if (d.flags[i] == CL_L) acc += cell_density<S>(d, d.fdst, i);
-        else if (d.flags[i] == CL_I) acc += d.m[i];
+        if (clsv(d, i) == CL_L) acc += cell_density<S>(d, d.fdst, i);
+        else if (clsv(d, i) == CL_I) acc += d.m[i];
         d.cmark[i] = 0;
     }
     __shared__ double sh[REMAP_THREADS / 32];
@@ -1277,9 +1319,17 @@ template <int S>
 __global__ void __launch_bounds__(256) k_mass_partial(Dev d) {
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)gridDim.x * blockDim.x) {
-        int c = d.flags[i];
-        if (c == CL_L) acc += cell_density<S>(d, d.fsrc, i);
-        else if (c == CL_I) acc += d.m[i];
+        int c = clsv(d, i);
+        if (c == CL_L) {
+            acc += cell_density<S>(d, d.fsrc, i);
+            // closed interface layer (Sec. 2.2): no liquid cell touches gas
+            int x, y, z;
+            coords(d, i, x, y, z);
+            for (int q = 1; q < Q; ++q)
+                if (cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q))) == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
+        } else if (c == CL_I) {
+            acc += d.m[i];
+        }
     }
     __shared__ double sh[8];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -1304,7 +1354,7 @@ __global__ void k_read_fields(Dev d, unsigned mask, uint8_t *flags, double *fill
                               double *f) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= d.N) return;
-    int c = d.flags[i];
+    int c = clsv(d, i);
     bool fluid = c == CL_L || c == CL_I;
     double u[3] = {0.0, 0.0, 0.0};
     double r = fluid ? cell_rho_u<S>(d, d.fsrc, i, u) : 0.0;
@@ -1328,10 +1378,12 @@ template <int S> struct Launch {
                            cudaStream_t st) {
         unsigned blocks = (unsigned)((d.N + 255) / 256);
         k_init<S><<<blocks, 256, 0, st>>>(d, flags, fill, rho, vel);
+        k_nb_all<<<LIST_BLOCKS * 4, 256, 0, st>>>(d);
     }
     static void body_prepare(const Dev &d, int b, cudaStream_t st) { k_body_prepare<<<1, 32, 0, st>>>(d, b); }
     static void map_body(const Dev &d, int b, int book, cudaStream_t st) {
         k_map_body<S><<<FORCE_BLOCKS, 256, 0, st>>>(d, b, book);
+        k_nb_all<<<LIST_BLOCKS * 4, 256, 0, st>>>(d);
     }
     static void liquid_mass(const Dev &d, cudaStream_t st) {
         k_mass_partial<S><<<LIST_BLOCKS, 256, 0, st>>>(d);
@@ -1383,14 +1435,16 @@ template <int S> struct Launch {
         mark();
         if (d.nb > 0) k_remap_resolve<S><<<1, REMAP_THREADS, 0, st>>>(d);
         mark();
-        return d.nb > 0 ? 14 : 9;  // kernels (the counter reset is a memset node)
+        if (d.nb > 0) k_nb_update<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        mark();
+        return d.nb > 0 ? 15 : 9;  // kernels (the counter reset is a memset node)
     }
 };
 
 inline const char *const *kernel_names() {
     static const char *const n[] = {"reset_counters", "forces", "liquid", "interface", "conv_filled",
                                     "conv_emptied",    "conv_init", "conv_flags", "conv_claim", "conv_excess",
-                                    "conv_finish",     "bodies",  "remap_cover", "remap_pending", "remap_resolve"};
+                                    "conv_finish",     "bodies",  "remap_cover", "remap_pending", "remap_resolve", "nb_update"};
     return n;
 }
 
@@ -1402,7 +1456,7 @@ template <int S> KernelSet make_kernel_set() {
     k.step = &Launch<S>::step;
     k.liquid_mass = &Launch<S>::liquid_mass;
     k.read_fields = &Launch<S>::read_fields;
-    k.nkernels = 15;
+    k.nkernels = 16;
     k.names = kernel_names();
     return k;
 }
