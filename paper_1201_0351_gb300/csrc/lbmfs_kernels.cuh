@@ -64,7 +64,10 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 constexpr double NORMAL_DEADBAND = 1e-3;
 constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2015
 #ifndef LBMFS_BULK_MINB
-#define LBMFS_BULK_MINB 1  // minimum resident blocks per SM asked of ptxas for the bulk kernel
+#define LBMFS_BULK_MINB 8  // resident blocks per SM asked of ptxas for the bulk kernel (64 registers)
+#endif
+#ifndef LBMFS_BULK_ZB
+#define LBMFS_BULK_ZB 4    // z-planes per bulk-kernel block
 #endif
 constexpr float F16_SCALE = 1024.0f;
 constexpr float F16_INV_SCALE = 1.0f / 1024.0f;
@@ -553,52 +556,39 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
         }
     }
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    long long n = range_count(lo, hi);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    long long n = range_count(lo, hi) * (Q - 1);  // (cell, direction) pairs
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int q = 1 + (int)(t % (Q - 1));
         int x, y, z;
-        range_cell(d, lo, hi, k, x, y, z);
+        range_cell(d, lo, hi, t / (Q - 1), x, y, z);
+        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
         int cl = clsv(d, i);
         if (cl == CL_O) continue;
         double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
-        bool have_rho = false;
-        double rho_x = 0.0;
+        double cuw = link_cuw(d, b, x, y, z, q);
+        int qb = opp(q);
+        double inner;
+        if (cl == CL_G) {
+            inner = wd(q) * d.rho_g;
+        } else {
+            double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
+            double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
+            double C = cuw == 0.0 ? phi_x * 0.0 : phi_x * (((3.0 * wd(q)) * cell_density<S>(d, d.fsrc, i)) * cuw);
+            inner = (A + B) + C;
+        }
+        double g = 2.0 * inner;
         double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
                        min_image(d, (z + 0.5) - b.o[2], 2)};
-#pragma unroll 1
-        for (int q = 1; q < Q; ++q) {
-            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
-            double cuw = link_cuw(d, b, x, y, z, q);
-            int qb = opp(q);
-            double inner;
-            if (cl == CL_G) {
-                inner = wd(q) * d.rho_g;
-            } else {
-                double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
-                double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
-                double C;
-                if (cuw == 0.0) {
-                    C = phi_x * 0.0;
-                } else {
-                    if (!have_rho) {
-                        rho_x = cell_density<S>(d, d.fsrc, i);
-                        have_rho = true;
-                    }
-                    C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
-                }
-                inner = (A + B) + C;
-            }
-            double g = 2.0 * inner;
-            double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
-            acc[0] += F0;
-            acc[1] += F1;
-            acc[2] += F2;
-            acc[3] += r[1] * F2 - r[2] * F1;
-            acc[4] += r[2] * F0 - r[0] * F2;
-            acc[5] += r[0] * F1 - r[1] * F0;
-            acc[6] += fabs(g);
-        }
+        double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+        acc[0] += F0;
+        acc[1] += F1;
+        acc[2] += F2;
+        acc[3] += r[1] * F2 - r[2] * F1;
+        acc[4] += r[2] * F0 - r[0] * F2;
+        acc[5] += r[0] * F1 - r[1] * F0;
+        acc[6] += fabs(g);
     }
     // deterministic block reduction (fixed shuffle tree, then warps in order)
     __shared__ double sh[8][7];
@@ -638,11 +628,23 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
 
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
 template <int S>
+__device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
+
+// one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
+// consecutive z (amortises the launch of blocks that meet only gas)
+template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid(Dev d) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    int z0 = blockIdx.z * LBMFS_BULK_ZB;
+    int z1 = min(z0 + LBMFS_BULK_ZB, d.nz);
+    for (int z = z0; z < z1; ++z) liquid_cell<S>(d, x, y, z);
+}
+
+template <int S>
+__device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     using P = Sto<S>;
     using R = typename P::R;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
     bool in = x < d.nx;
     long long i = (long long)(in ? x : 0) + (long long)d.nx * (y + (long long)d.ny * z);
     int c = in ? (int)d.flags[i] : 0;
@@ -1409,7 +1411,8 @@ template <int S> struct Launch {
         mark();
         if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
         mark();
-        k_liquid<S><<<dim3((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, d.nz), BULK_THREADS, 0, st>>>(d);
+        k_liquid<S><<<dim3((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB),
+                      BULK_THREADS, 0, st>>>(d);
         mark();
         k_interface<S><<<LIST_BLOCKS * 2, 128, 0, st>>>(d);
         mark();
