@@ -69,21 +69,33 @@ constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2
 #ifndef LBMFS_BULK_ZB
 #define LBMFS_BULK_ZB 4    // z-planes per bulk-kernel block
 #endif
+#ifndef LBMFS_ST_CS
+#define LBMFS_ST_CS 0      // population stores with the evict-first (streaming) hint
+#endif
 constexpr float F16_SCALE = 1024.0f;
 constexpr float F16_INV_SCALE = 1.0f / 1024.0f;
 constexpr int CL_WALL = 256;
 
 // ----------------------------------------------------------------- storage
+// population loads / stores (tuning knob: evict-first stores)
+template <class T> __device__ __forceinline__ T pop_ld(const T *p) { return *p; }
+template <class T> __device__ __forceinline__ void pop_st(T *p, T v) {
+#if LBMFS_ST_CS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
 template <int S> struct Sto;
 
 template <> struct Sto<0> {
     using R = double;
     static constexpr bool shifted = false;
     static __device__ __forceinline__ double ld(const void *g, int q, long long i, long long N) {
-        return reinterpret_cast<const double *>(g)[(long long)q * N + i];
+        return pop_ld(reinterpret_cast<const double *>(g) + ((long long)q * N + i));
     }
     static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, double v) {
-        reinterpret_cast<double *>(g)[(long long)q * N + i] = v;
+        pop_st(reinterpret_cast<double *>(g) + ((long long)q * N + i), v);
     }
     // value of f_q as double
     static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
@@ -101,10 +113,10 @@ template <> struct Sto<1> {
     using R = float;
     static constexpr bool shifted = true;
     static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
-        return reinterpret_cast<const float *>(g)[(long long)q * N + i];
+        return pop_ld(reinterpret_cast<const float *>(g) + ((long long)q * N + i));
     }
     static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, float v) {
-        reinterpret_cast<float *>(g)[(long long)q * N + i] = v;
+        pop_st(reinterpret_cast<float *>(g) + ((long long)q * N + i), v);
     }
     static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
         return wd(q) + (double)ld(g, q, i, N);
@@ -129,8 +141,8 @@ template <> struct Sto<2> {
         return reinterpret_cast<const __half *>(reinterpret_cast<const float *>(g) + N);
     }
     static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
-        if (q == 0) return reinterpret_cast<const float *>(g)[i];
-        return __half2float(hp(g, N)[(long long)(q - 1) * N + i]) * F16_INV_SCALE;
+        if (q == 0) return pop_ld(reinterpret_cast<const float *>(g) + i);
+        return __half2float(pop_ld(hp(g, N) + ((long long)(q - 1) * N + i))) * F16_INV_SCALE;
     }
     static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
         return wd(q) + (double)ld(g, q, i, N);
@@ -143,10 +155,10 @@ template <> struct Sto<2> {
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
             __half hq = __float2half_rn(dv[q] * F16_SCALE);
-            h[(long long)(q - 1) * N + i] = hq;
+            pop_st(h + ((long long)(q - 1) * N + i), hq);
             rest -= __half2float(hq) * F16_INV_SCALE;
         }
-        reinterpret_cast<float *>(g)[i] = rest;
+        pop_st(reinterpret_cast<float *>(g) + i, rest);
     }
     static __device__ __forceinline__ void st_cell(void *g, long long i, long long N, const double *f) {
         double drho = 0.0;
@@ -556,43 +568,64 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
         }
     }
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    long long n = range_count(lo, hi) * (Q - 1);  // (cell, direction) pairs
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        int q = 1 + (int)(t % (Q - 1));
-        int x, y, z;
-        range_cell(d, lo, hi, t / (Q - 1), x, y, z);
-        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
-        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-        int cl = clsv(d, i);
-        if (cl == CL_O) continue;
-        double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
-        double cuw = link_cuw(d, b, x, y, z, q);
-        int qb = opp(q);
-        double inner;
-        if (cl == CL_G) {
-            inner = wd(q) * d.rho_g;
-        } else {
-            double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
-            double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
-            double C = cuw == 0.0 ? phi_x * 0.0 : phi_x * (((3.0 * wd(q)) * cell_density<S>(d, d.fsrc, i)) * cuw);
-            inner = (A + B) + C;
+    // z-planes over blocks, (x, y) over the block's 32 x 8 threads; only cells
+    // next to an obstacle (neighbour-obstacle bit) can hold links
+    for (int zz = lo[2] + (int)blockIdx.x; zz < hi[2]; zz += gridDim.x) {
+        int z = zz < 0 ? zz + d.nz : (zz >= d.nz ? zz - d.nz : zz);
+        for (int yy = lo[1] + (int)threadIdx.y; yy < hi[1]; yy += blockDim.y) {
+            int y = yy < 0 ? yy + d.ny : (yy >= d.ny ? yy - d.ny : yy);
+            for (int xx = lo[0] + (int)threadIdx.x; xx < hi[0]; xx += blockDim.x) {
+                int x = xx < 0 ? xx + d.nx : (xx >= d.nx ? xx - d.nx : xx);
+                long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+                int fb = d.flags[i];
+                int cl = fb & CL_MASK;
+                if (!(fb & NB_OBST) || cl == CL_O) continue;
+                double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
+                double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
+                               min_image(d, (z + 0.5) - b.o[2], 2)};
+                bool have_rho = false;
+                double rho_x = 0.0;
+#pragma unroll 1
+                for (int q = 1; q < Q; ++q) {
+                    long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                    if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
+                    double cuw = link_cuw(d, b, x, y, z, q);
+                    int qb = opp(q);
+                    double inner;
+                    if (cl == CL_G) {
+                        inner = wd(q) * d.rho_g;
+                    } else {
+                        double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
+                        double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
+                        double C;
+                        if (cuw == 0.0) {
+                            C = phi_x * 0.0;
+                        } else {
+                            if (!have_rho) {
+                                rho_x = cell_density<S>(d, d.fsrc, i);
+                                have_rho = true;
+                            }
+                            C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
+                        }
+                        inner = (A + B) + C;
+                    }
+                    double g = 2.0 * inner;
+                    double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+                    acc[0] += F0;
+                    acc[1] += F1;
+                    acc[2] += F2;
+                    acc[3] += r[1] * F2 - r[2] * F1;
+                    acc[4] += r[2] * F0 - r[0] * F2;
+                    acc[5] += r[0] * F1 - r[1] * F0;
+                    acc[6] += fabs(g);
+                }
+            }
         }
-        double g = 2.0 * inner;
-        double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
-                       min_image(d, (z + 0.5) - b.o[2], 2)};
-        double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
-        acc[0] += F0;
-        acc[1] += F1;
-        acc[2] += F2;
-        acc[3] += r[1] * F2 - r[2] * F1;
-        acc[4] += r[2] * F0 - r[0] * F2;
-        acc[5] += r[0] * F1 - r[1] * F0;
-        acc[6] += fabs(g);
     }
     // deterministic block reduction (fixed shuffle tree, then warps in order)
     __shared__ double sh[8][7];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
         double v = acc[c];
@@ -600,10 +633,10 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
         if (lane == 0) sh[wid][c] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 7) {
+    if (tid < 7) {
         double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
-        d.part[((long long)bi * FORCE_BLOCKS + blockIdx.x) * 7 + threadIdx.x] = v;
+        for (int w = 0; w < 8; ++w) v += sh[w][tid];
+        d.part[((long long)bi * FORCE_BLOCKS + blockIdx.x) * 7 + tid] = v;
     }
 }
 
@@ -1409,7 +1442,7 @@ template <int S> struct Launch {
         mark();
         cudaMemsetAsync(d.cnt, 0, WL_COUNT * sizeof(uint32_t), st);
         mark();
-        if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
+        if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), dim3(32, 8), 0, st>>>(d);
         mark();
         k_liquid<S><<<dim3((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB),
                       BULK_THREADS, 0, st>>>(d);
