@@ -583,41 +583,90 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
                 double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
                 double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
                                min_image(d, (z + 0.5) - b.o[2], 2)};
-                bool have_rho = false;
-                double rho_x = 0.0;
+                if constexpr (S == 0) {
+                    // double, in the order of the plain restatement
+                    bool have_rho = false;
+                    double rho_x = 0.0;
 #pragma unroll 1
-                for (int q = 1; q < Q; ++q) {
-                    long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                    if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
-                    double cuw = link_cuw(d, b, x, y, z, q);
-                    int qb = opp(q);
-                    double inner;
-                    if (cl == CL_G) {
-                        inner = wd(q) * d.rho_g;
-                    } else {
-                        double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
-                        double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
-                        double C;
-                        if (cuw == 0.0) {
-                            C = phi_x * 0.0;
+                    for (int q = 1; q < Q; ++q) {
+                        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
+                        double cuw = link_cuw(d, b, x, y, z, q);
+                        int qb = opp(q);
+                        double inner;
+                        if (cl == CL_G) {
+                            inner = wd(q) * d.rho_g;
                         } else {
-                            if (!have_rho) {
-                                rho_x = cell_density<S>(d, d.fsrc, i);
-                                have_rho = true;
+                            double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
+                            double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
+                            double C;
+                            if (cuw == 0.0) {
+                                C = phi_x * 0.0;
+                            } else {
+                                if (!have_rho) {
+                                    rho_x = cell_density<S>(d, d.fsrc, i);
+                                    have_rho = true;
+                                }
+                                C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
                             }
-                            C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
+                            inner = (A + B) + C;
                         }
-                        inner = (A + B) + C;
+                        double g = 2.0 * inner;
+                        double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+                        acc[0] += F0;
+                        acc[1] += F1;
+                        acc[2] += F2;
+                        acc[3] += r[1] * F2 - r[2] * F1;
+                        acc[4] += r[2] * F0 - r[0] * F2;
+                        acc[5] += r[0] * F1 - r[1] * F0;
+                        acc[6] += fabs(g);
                     }
-                    double g = 2.0 * inner;
-                    double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
-                    acc[0] += F0;
-                    acc[1] += F1;
-                    acc[2] += F2;
-                    acc[3] += r[1] * F2 - r[2] * F1;
-                    acc[4] += r[2] * F0 - r[0] * F2;
-                    acc[5] += r[0] * F1 - r[1] * F0;
-                    acc[6] += fabs(g);
+                } else {
+                    // reduced-precision storage: link terms in float (the
+                    // populations are float), sums in double
+                    float phf = (float)phi_x, rhog = (float)d.rho_g;
+                    float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+                    float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
+                    float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
+                    float rho_x = -1.0f;
+#pragma unroll 1
+                    for (int q = 1; q < Q; ++q) {
+                        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
+                        int qb = opp(q);
+                        // u_w at the link midpoint: r + c_qbar / 2 from the body centre
+                        float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb), pz = rf[2] + 0.5f * cz(qb);
+                        float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
+                        float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
+                        float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
+                        float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+                        float inner;
+                        if (cl == CL_G) {
+                            inner = wf(q) * rhog;
+                        } else {
+                            float fbar = wf(qb) + Sto<S>::ld(d.fsrc, qb, i, d.N);
+                            float C = 0.0f;
+                            if (cuw != 0.0f) {
+                                if (rho_x < 0.0f) {
+                                    float dr = 0.0f;
+#pragma unroll
+                                    for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
+                                    rho_x = 1.0f + dr;
+                                }
+                                C = phf * (3.0f * wf(q) * rho_x * cuw);
+                            }
+                            inner = phf * fbar + (1.0f - phf) * (wf(q) * rhog) + C;
+                        }
+                        float g = 2.0f * inner;
+                        float F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+                        acc[0] += (double)F0;
+                        acc[1] += (double)F1;
+                        acc[2] += (double)F2;
+                        acc[3] += (double)(rf[1] * F2 - rf[2] * F1);
+                        acc[4] += (double)(rf[2] * F0 - rf[0] * F2);
+                        acc[5] += (double)(rf[0] * F1 - rf[1] * F0);
+                        acc[6] += (double)fabsf(g);
+                    }
                 }
             }
         }
