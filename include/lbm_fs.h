@@ -192,6 +192,29 @@ lbm_fs_status lbm_fs_kernel_times(lbm_fs *h, int32_t nsteps, double *ms,
 const char *lbm_fs_last_error_string(void);
 int32_t lbm_fs_version(void);
 
+/* Liquid mass without allocating: sum over liquid and interface cells of the
+ * per-cell mass, for callers that cannot allocate device memory (a host that
+ * owns a fixed memory budget, work recorded inside a CUDA graph capture, or a
+ * loop that must not block on an allocator).  The paper has no counterpart:
+ * this is a library-level variant of the reduction behind lbm_fs_stats.
+ *   flags: device pointer, n class bytes (LBM_FS_FIELD_FLAGS layout);
+ *   mass:  device pointer, n doubles (LBM_FS_FIELD_MASS layout);
+ *   out:   device pointer, receives one double;
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Block partial sums live in a fixed 512 KiB device array of the library
+ * (held by every GPU that loads the library until exit), so n is limited to
+ * 268435456 cells; larger n, n < 0 or a null pointer give LBM_FS_EINVAL.  The
+ * first call on a device looks up that array's device address (set-up with the
+ * device current); make that first call before any stream capture.  Every call
+ * on a device shares the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (different streams, no ordering) race and may return
+ * wrong sums.  No cudaMalloc / cudaFree or allocating routine is called.  The
+ * call is asynchronous; errors of the launch are returned, the error text is
+ * in lbm_fs_noalloc_last_error_string(). */
+lbm_fs_status lbm_fs_liquid_mass_noalloc(const uint8_t *flags, const double *mass, int64_t n,
+                                         double *out, void *stream);
+const char *lbm_fs_noalloc_last_error_string(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,7 +58,7 @@ class lbm_fs_stats_t(C.Structure):
 
 EXPORTS = ("lbm_fs_create", "lbm_fs_destroy", "lbm_fs_add_box", "lbm_fs_step", "lbm_fs_forces", "lbm_fs_body_state",
            "lbm_fs_read_fields", "lbm_fs_stats", "lbm_fs_sync", "lbm_fs_kernel_times", "lbm_fs_last_error_string",
-           "lbm_fs_version")
+           "lbm_fs_version", "lbm_fs_liquid_mass_noalloc", "lbm_fs_noalloc_last_error_string")
 
 _lib = None
 
@@ -96,8 +96,11 @@ def load(build_if_needed: bool = True):
     lib.lbm_fs_last_error_string.restype = C.c_char_p
     lib.lbm_fs_last_error_string.argtypes = []
     lib.lbm_fs_version.restype = I32
+    lib.lbm_fs_liquid_mass_noalloc.argtypes = [P, P, C.c_int64, P, P]
+    lib.lbm_fs_noalloc_last_error_string.restype = C.c_char_p
+    lib.lbm_fs_noalloc_last_error_string.argtypes = []
     for name in EXPORTS:
-        if name not in ("lbm_fs_last_error_string", "lbm_fs_version"):
+        if name not in ("lbm_fs_last_error_string", "lbm_fs_version", "lbm_fs_noalloc_last_error_string"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -165,6 +168,15 @@ def lbm_fs_kernel_times(h, nsteps: int):
     nk = C.c_int32(0)
     _check(load().lbm_fs_kernel_times(h, int(nsteps), ms, names, cap, C.byref(nk)), "lbm_fs_kernel_times")
     return {names[k].decode(): ms[k] for k in range(nk.value)}
+
+
+def lbm_fs_liquid_mass_noalloc(flags_dev: int, mass_dev: int, n: int, out_dev: int, stream: int = 0):
+    """Liquid mass from device arrays without any device allocation (see the
+    C declaration for the limits and the shared fixed scratch)."""
+    code = load().lbm_fs_liquid_mass_noalloc(C.c_void_p(flags_dev), C.c_void_p(mass_dev), int(n),
+                                             C.c_void_p(out_dev), C.c_void_p(stream) if stream else None)
+    if code != LBM_FS_OK:
+        raise LbmFsError(code, "lbm_fs_liquid_mass_noalloc", load().lbm_fs_noalloc_last_error_string().decode())
 
 
 # ------------------------------------------------------------ convenience

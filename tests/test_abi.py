@@ -32,7 +32,8 @@ def test_every_declared_function_is_exported():
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
     # the Python binding carries the same names
-    assert all(hasattr(lbm_fs, n) for n in names if n not in ("lbm_fs_last_error_string", "lbm_fs_version"))
+    assert all(hasattr(lbm_fs, n) for n in names if n not in ("lbm_fs_last_error_string", "lbm_fs_version",
+                                                               "lbm_fs_noalloc_last_error_string"))
 
 
 def _params(**kw):
@@ -76,3 +77,11 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.lbm_fs_destroy(None) == lbm_fs.LBM_FS_EINVAL
     assert b"null" in lib.lbm_fs_last_error_string()
 
+
+def test_noalloc_entry_rejects_bad_sizes_on_host():
+    lib = lbm_fs.load()
+    buf = ctypes.c_double(0.0)
+    p = ctypes.cast(ctypes.pointer(buf), ctypes.c_void_p)
+    assert lib.lbm_fs_liquid_mass_noalloc(p, p, -1, p, None) == lbm_fs.LBM_FS_EINVAL
+    assert lib.lbm_fs_liquid_mass_noalloc(p, p, 268435457, p, None) == lbm_fs.LBM_FS_EINVAL
+    assert lib.lbm_fs_liquid_mass_noalloc(None, p, 10, p, None) == lbm_fs.LBM_FS_EINVAL
