@@ -622,9 +622,12 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
                         acc[6] += fabs(g);
                     }
                 } else {
-                    // reduced-precision storage: link terms in float (the
-                    // populations are float), sums in double
-                    float phf = (float)phi_x, rhog = (float)d.rho_g;
+                    // reduced-precision storage: the link term is split into the
+                    // uniform gas-pressure part 2 w_q rho_G (double) and the small
+                    // remainder 2 (phi (f_qbar - w_q rho_G) + moving-wall part),
+                    // computed in float from the stored deviations f - w
+                    float phf = (float)phi_x;
+                    float wrg1 = (float)(1.0 - d.rho_g);
                     float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
                     float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
                     float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
@@ -634,17 +637,15 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
                         long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
                         if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
                         int qb = opp(q);
-                        // u_w at the link midpoint: r + c_qbar / 2 from the body centre
-                        float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb), pz = rf[2] + 0.5f * cz(qb);
-                        float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
-                        float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
-                        float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
-                        float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-                        float inner;
-                        if (cl == CL_G) {
-                            inner = wf(q) * rhog;
-                        } else {
-                            float fbar = wf(qb) + Sto<S>::ld(d.fsrc, qb, i, d.N);
+                        double s0 = 2.0 * (wd(q) * d.rho_g);
+                        float gdev = 0.0f;
+                        if (cl != CL_G) {
+                            // u_w at the link midpoint, r + c_qbar / 2 from the body centre
+                            float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb), pz = rf[2] + 0.5f * cz(qb);
+                            float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
+                            float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
+                            float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
+                            float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
                             float C = 0.0f;
                             if (cuw != 0.0f) {
                                 if (rho_x < 0.0f) {
@@ -655,17 +656,25 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
                                 }
                                 C = phf * (3.0f * wf(q) * rho_x * cuw);
                             }
-                            inner = phf * fbar + (1.0f - phf) * (wf(q) * rhog) + C;
+                            float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
+                            gdev = 2.0f * (phf * dev + C);
                         }
-                        float g = 2.0f * inner;
-                        float F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+                        // static part in double
+                        if (cx(qb)) acc[0] += cx(qb) * s0;
+                        if (cy(qb)) acc[1] += cy(qb) * s0;
+                        if (cz(qb)) acc[2] += cz(qb) * s0;
+                        acc[3] += s0 * (r[1] * cz(qb) - r[2] * cy(qb));
+                        acc[4] += s0 * (r[2] * cx(qb) - r[0] * cz(qb));
+                        acc[5] += s0 * (r[0] * cy(qb) - r[1] * cx(qb));
+                        // remainder in float
+                        float F0 = cx(qb) * gdev, F1 = cy(qb) * gdev, F2 = cz(qb) * gdev;
                         acc[0] += (double)F0;
                         acc[1] += (double)F1;
                         acc[2] += (double)F2;
                         acc[3] += (double)(rf[1] * F2 - rf[2] * F1);
                         acc[4] += (double)(rf[2] * F0 - rf[0] * F2);
                         acc[5] += (double)(rf[0] * F1 - rf[1] * F0);
-                        acc[6] += (double)fabsf(g);
+                        acc[6] += fabs(s0 + (double)gdev);
                     }
                 }
             }
@@ -789,29 +798,29 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
         long long i = d.list[WL_IFACE][it];
         int x, y, z;
         coords(d, i, x, y, z);
-        long long src[Q];
-        int scl[Q];
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            scl[q] = cls(d, src[q]);
-        }
-        // normal n = -grad(phi), central differences
         double own_phi = d.phisrc[i];
-        double nv[3];
-        {
-            double pm = fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi);
-            double pp = fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi);
-            nv[0] = 0.5 * (pm - pp);
-            pm = fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi);
-            pp = fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi);
-            nv[1] = 0.5 * (pm - pp);
-            pm = fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi);
-            pp = fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi);
-            nv[2] = 0.5 * (pm - pp);
-        }
         double m_new;
         if constexpr (!P::shifted) {
+            long long src[Q];
+            int scl[Q];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                scl[q] = cls(d, src[q]);
+            }
+            // normal n = -grad(phi), central differences
+            double nv[3];
+            {
+                double pm = fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi);
+                double pp = fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi);
+                nv[0] = 0.5 * (pm - pp);
+                pm = fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi);
+                pp = fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi);
+                nv[1] = 0.5 * (pm - pp);
+                pm = fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi);
+                pp = fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi);
+                nv[2] = 0.5 * (pm - pp);
+            }
             double fo[Q], fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
@@ -878,6 +887,13 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
             wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
         } else {
+            float phx = (float)own_phi;
+            float nv0 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi) -
+                                (float)fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi));
+            float nv1 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi) -
+                                (float)fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi));
+            float nv2 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi) -
+                                (float)fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi));
             float fo[Q], fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
@@ -893,47 +909,53 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
             float ux = j0 / rx - (float)d.a[0], uy = j1 / rx - (float)d.a[1], uz = j2 / rx - (float)d.a[2];
             float drg = (float)(d.rho_g - 1.0);
             fp[0] = fo[0];
+            unsigned solid = 0;  // directions whose source is an obstacle or a wall
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 int qb = opp(q);
-                if (scl[q] == CL_WALL || scl[q] == CL_O) {
-                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q) : 0.0;
-                    fp[q] = fo[qb] + (float)(6.0 * wd(q) * cuw) * rx;
-                } else if (scl[q] == CL_G) {
+                long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                int ns = cls(d, si);
+                if (ns == CL_WALL || ns == CL_O) {
+                    solid |= 1u << q;
+                    float cuw = ns == CL_O ? (float)link_cuw(d, d.bodies[d.bid[si]], x, y, z, q) : 0.0f;
+                    fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
+                } else if (ns == CL_G) {
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
                 } else {
-                    fp[q] = P::ld(d.fsrc, q, src[q], N);
+                    fp[q] = P::ld(d.fsrc, q, si, N);
                 }
             }
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
-                if (cn < -NORMAL_DEADBAND && scl[q] != CL_O && scl[q] != CL_WALL) {
+                float cn = cx(q) * nv0 + cy(q) * nv1 + cz(q) * nv2;
+                if (cn < -(float)NORMAL_DEADBAND && !(solid & (1u << q))) {
                     int qb = opp(q);
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
                 }
             }
-            double dm = 0.0;
+            // Sec. 2.2 mass exchange; each link term is computed identically
+            // (up to sign) by both cells, so the exchange stays conservative
+            float dm = 0.0f;
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 int qb = opp(q);
                 long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
                 int yc = cls(d, yi);
                 if (yc == CL_L) {
-                    dm += (double)(P::ld(d.fsrc, qb, yi, N) - fo[q]);
+                    dm += P::ld(d.fsrc, qb, yi, N) - fo[q];
                 } else if (yc == CL_I) {
-                    double wgt = 0.5 * (own_phi + d.phisrc[yi]);
-                    dm += wgt * (double)(P::ld(d.fsrc, qb, yi, N) - fo[q]);
+                    float wgt = 0.5f * (phx + (float)d.phisrc[yi]);
+                    dm += wgt * (P::ld(d.fsrc, qb, yi, N) - fo[q]);
                 }
             }
-            m_new = d.m[i] + dm;
+            m_new = d.m[i] + (double)dm;
             float dn[Q], rho;
             float dr = collide_f(d, fp, dn, rho);
             P::st_dev(d.fdst, i, N, dn, dr);
-            double r = 0.0;
+            float drs = 0.0f;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) r += (double)P::ld(d.fdst, q, i, N);
-            r += 1.0;
+            for (int q = 0; q < Q; ++q) drs += P::ld(d.fdst, q, i, N);
+            double r = 1.0 + (double)drs;
             double phin = m_new / r;
             d.m[i] = m_new;
             d.phidst[i] = phin;
