@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % of HBM roofline, FP32/FP16-stored vs FP64 plain at stated error"
 BYTES_PER_FLUID = {"f64": 38 * 8, "f32": 38 * 4, "f16s": 80}
+C_BODY_BYTES = 8 * (3 + 3 + 1 + 3 + 4 + 3 + 3)  # one lbm_fs_body_state_t
 DTYPE = {"f64": "f64", "f32": "f32", "f16s": "f16s/f32"}
 
 
@@ -147,8 +148,8 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
                 liquid_gbs=liquid_bytes / (kt.get("liquid", float("nan")) / kernel_steps * 1e-3) / 1e9,
                 kernel_share={k: v / total_k for k, v in kt.items() if total_k > 0},
                 launches=launches, status=st["status"], n_fluid=(n_liq + n_if), n_interface=n_if,
-                mass_resid=(st["liquid_mass"] - st["mass0"] - (st["uncovered"] - st["covered"] - st["lost_excess"]))
-                / st["mass0"])
+                mass_resid=(st["liquid_mass"] - st["mass0"] - (st["uncovered"] - st["covered"] - st["lost_excess"]
+                                                               + st["wall_source"])) / st["mass0"])
 
 
 class _Null:
@@ -161,8 +162,9 @@ class _Null:
 
 def e2e_run(sc, storage, steps):
     """Through the public API with host buffers: create (uploads the initial
-    host arrays), then every step lbm_fs_step + lbm_fs_forces of all bodies
-    (device -> host read of the step's result), timed on the host clock."""
+    host arrays), then every step lbm_fs_step + lbm_fs_body_states of all
+    bodies (device -> host read of the step's forces, torques and poses, as a
+    host-side rigid-body coupling would do), timed on the host clock."""
     import torch
 
     from paper_1201_0351_gb300 import lbm_fs
@@ -170,28 +172,33 @@ def e2e_run(sc, storage, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim = lbm_fs.Simulation(sc, storage=storage, use_graphs=True, host_init=True)
+    states = (lbm_fs.lbm_fs_body_state_t * max(sim.nbodies, 1))()
     for _ in range(steps):
         sim.step(1)
-        for b in range(sim.nbodies):
-            lbm_fs.lbm_fs_forces(sim.h, b)
+        lbm_fs.lbm_fs_body_states(sim.h, 0, sim.nbodies, states)
     sim.sync()
     t1 = time.perf_counter()
     sim.close()
     n = sc.nx * sc.ny * sc.nz
     h2d = sc.flags.nbytes + sc.fill.nbytes + sc.rho.nbytes
-    d2h = sim.nbodies * 8 * (3 + 3 + 3 + 4)
+    d2h = sim.nbodies * C_BODY_BYTES
     return dict(value=n * steps / (t1 - t0) / 1e6, unit="MLUPS", h2d_bytes_per_step=h2d // steps,
                 d2h_bytes_per_step=d2h)
 
 
 def cpu_baseline(sc_full, target_s=15.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: a 192 x 96 column-crop of the tank (full depth, walls on the cut),
-    as many steps as fit in about target_s seconds."""
+    workload: a 192 x 96 column window of the tank centred on its first box
+    (full depth, walls on the cut), as many steps as fit in about target_s
+    seconds."""
     import oracle
     from paper_1201_0351_gb300 import inputs
 
-    sc = inputs.crop(sc_full, min(192, sc_full.nx), min(96, sc_full.ny))
+    wx, wy = min(192, sc_full.nx), min(96, sc_full.ny)
+    b0 = sc_full.boxes[0] if sc_full.boxes else None
+    x0 = 0 if b0 is None else int(min(max(b0.center[0] - wx / 2, 0), sc_full.nx - wx))
+    y0 = 0 if b0 is None else int(min(max(b0.center[1] - wy / 2, 0), sc_full.ny - wy))
+    sc = inputs.crop(sc_full, wx, wy, x0=x0, y0=y0)
     t0 = time.perf_counter()
     sim = oracle.OracleSim(sc)
     t_setup = time.perf_counter() - t0

@@ -170,6 +170,10 @@ lbm_fs_status lbm_fs_step(lbm_fs *h, int32_t nsteps);
 lbm_fs_status lbm_fs_forces(lbm_fs *h, int32_t id, double F[3], double T[3],
                             double center[3], double quat[4]);
 lbm_fs_status lbm_fs_body_state(lbm_fs *h, int32_t id, lbm_fs_body_state_t *out);
+/* Synchronises once and copies the states of bodies first .. first+count-1 into
+ * out[0 .. count-1] (one device-to-host copy: the per-step read of a coupled
+ * host-side rigid-body engine). */
+lbm_fs_status lbm_fs_body_states(lbm_fs *h, int32_t first, int32_t count, lbm_fs_body_state_t *out);
 
 /* Synchronises and copies the selected fields into caller-owned buffers (host
  * or device, per dst_on_device), each sized as documented above. */

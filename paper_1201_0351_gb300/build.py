@@ -48,11 +48,12 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR,
+          csrc: str = CSRC) -> str:
     """Compile the library if any source is newer than it; returns its path.
-    extra_flags / out_dir build a variant elsewhere (tuning experiments)."""
+    extra_flags / out_dir / csrc build a variant elsewhere (tuning experiments)."""
     lib = os.path.join(out_dir, os.path.basename(LIB))
-    if not force and out_dir == OUT_DIR and not extra_flags and up_to_date():
+    if not force and out_dir == OUT_DIR and csrc == CSRC and not extra_flags and up_to_date():
         return LIB
     os.makedirs(out_dir, exist_ok=True)
     nv = nvcc()
@@ -61,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: s
     for unit, flags in UNITS.items():
         obj = os.path.join(out_dir, unit.replace(".cu", ".o"))
         objs.append(obj)
-        cmds.append([nv, *ARCH, *COMMON, *flags, *extra_flags, "-c", os.path.join(CSRC, unit), "-o", obj])
+        cmds.append([nv, *ARCH, "-I", csrc, *COMMON, *flags, *extra_flags, "-c", os.path.join(csrc, unit), "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

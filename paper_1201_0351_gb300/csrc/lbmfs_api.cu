@@ -371,6 +371,29 @@ lbm_fs_status lbm_fs_body_state(lbm_fs *h, int32_t id, lbm_fs_body_state_t *out)
     return read_status(h);
 }
 
+lbm_fs_status lbm_fs_body_states(lbm_fs *h, int32_t first, int32_t count, lbm_fs_body_state_t *out) {
+    lbm_fs_status s = check_handle(h);
+    if (s) return s;
+    if (first < 0 || count < 0 || first + count > h->nb || (count > 0 && !out))
+        return fail(LBM_FS_EINVAL, "bad body range%s");
+    if (count == 0) return read_status(h);
+    std::vector<Body> hb(count);
+    CK(cudaMemcpyAsync(hb.data(), h->d[0].bodies + first, sizeof(Body) * count, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int32_t b = 0; b < count; ++b) {
+        for (int k = 0; k < 3; ++k) {
+            out[b].F[k] = hb[b].F[k];
+            out[b].T[k] = hb[b].T[k];
+            out[b].center[k] = hb[b].o[k];
+            out[b].vel[k] = hb[b].v[k];
+            out[b].omega[k] = hb[b].w[k];
+        }
+        for (int k = 0; k < 4; ++k) out[b].quat[k] = hb[b].q[k];
+        out[b].S = hb[b].S;
+    }
+    return read_status(h);
+}
+
 lbm_fs_status lbm_fs_forces(lbm_fs *h, int32_t id, double F[3], double T[3], double center[3], double quat[4]) {
     lbm_fs_body_state_t bs;
     lbm_fs_status s = lbm_fs_body_state(h, id, &bs);

@@ -319,6 +319,13 @@ __device__ __forceinline__ double force_d(int q, double rho, const double *u, co
 
 template <int S>
 __device__ __forceinline__ double cell_density(const Dev &d, const void *g, long long i) {
+    if constexpr (S != 0) {
+        // deviations summed in float, as the collision does
+        float dr = 0.0f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) dr += Sto<S>::ld(g, q, i, d.N);
+        return 1.0 + (double)dr;
+    }
     double r = 0.0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) r += Sto<S>::ldf(g, q, i, d.N);
@@ -328,6 +335,22 @@ __device__ __forceinline__ double cell_density(const Dev &d, const void *g, long
 // density and the velocity of the last collision, sum c f / rho - a
 template <int S>
 __device__ __forceinline__ double cell_rho_u(const Dev &d, const void *g, long long i, double *u) {
+    if constexpr (S != 0) {
+        float dr = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            float v = Sto<S>::ld(g, q, i, d.N);
+            dr += v;
+            if (cx(q)) j0 += cx(q) * v;
+            if (cy(q)) j1 += cy(q) * v;
+            if (cz(q)) j2 += cz(q) * v;
+        }
+        float r = 1.0f + dr;
+        u[0] = (double)(j0 / r - (float)d.a[0]);
+        u[1] = (double)(j1 / r - (float)d.a[1]);
+        u[2] = (double)(j2 / r - (float)d.a[2]);
+        return 1.0 + (double)dr;
+    }
     double f[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = Sto<S>::ldf(g, q, i, d.N);

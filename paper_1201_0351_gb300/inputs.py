@@ -300,16 +300,22 @@ def wave_tank(nx: int = 768, ny: int = 384, nz: int = 256, nboxes: int = 16, see
                     1.0, 1e-2, flags, fill, rho, boxes, 2000)
 
 
-def crop(sc: Scenario, nx: int, ny: int, nz: Optional[int] = None, name: Optional[str] = None) -> Scenario:
-    """The lower-left nx x ny (x nz) part of a scenario, with the boxes whose centre
-    lies inside it (a bounded sample of a large workload; walls on the cut faces)."""
+def crop(sc: Scenario, nx: int, ny: int, nz: Optional[int] = None, name: Optional[str] = None,
+         x0: int = 0, y0: int = 0) -> Scenario:
+    """The nx x ny (x nz) window of a scenario starting at column (x0, y0), with
+    the boxes whose extent lies inside it, shifted to the window (a bounded
+    sample of a large workload; walls on the cut faces)."""
     nz = sc.nz if nz is None else nz
     sh = (sc.nz, sc.ny, sc.nx)
-    f3 = sc.flags.reshape(sh)[:nz, :ny, :nx]
-    p3 = sc.fill.reshape(sh)[:nz, :ny, :nx]
-    r3 = sc.rho.reshape(sh)[:nz, :ny, :nx]
-    boxes = [b for b in sc.boxes
-             if b.half[0] + 1 < b.center[0] < nx - b.half[0] - 1 and b.half[1] + 1 < b.center[1] < ny - b.half[1] - 1]
+    f3 = sc.flags.reshape(sh)[:nz, y0:y0 + ny, x0:x0 + nx]
+    p3 = sc.fill.reshape(sh)[:nz, y0:y0 + ny, x0:x0 + nx]
+    r3 = sc.rho.reshape(sh)[:nz, y0:y0 + ny, x0:x0 + nx]
+    boxes = []
+    for b in sc.boxes:
+        r = math.sqrt(sum(h * h for h in b.half))
+        cx_, cy_ = b.center[0] - x0, b.center[1] - y0
+        if r + 1 < cx_ < nx - r - 1 and r + 1 < cy_ < ny - r - 1:
+            boxes.append(dataclasses.replace(b, center=(cx_, cy_, b.center[2])))
     return dataclasses.replace(sc, name=name or sc.name + "_crop%dx%dx%d" % (nx, ny, nz), nx=nx, ny=ny, nz=nz,
                                periodic=sc.periodic & 0, flags=np.ascontiguousarray(f3).reshape(-1).copy(),
                                fill=np.ascontiguousarray(p3).reshape(-1).copy(),

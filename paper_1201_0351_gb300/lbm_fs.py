@@ -57,6 +57,7 @@ class lbm_fs_stats_t(C.Structure):
 
 
 EXPORTS = ("lbm_fs_create", "lbm_fs_destroy", "lbm_fs_add_box", "lbm_fs_step", "lbm_fs_forces", "lbm_fs_body_state",
+           "lbm_fs_body_states",
            "lbm_fs_read_fields", "lbm_fs_stats", "lbm_fs_sync", "lbm_fs_kernel_times", "lbm_fs_last_error_string",
            "lbm_fs_version", "lbm_fs_liquid_mass_noalloc", "lbm_fs_noalloc_last_error_string")
 
@@ -89,6 +90,7 @@ def load(build_if_needed: bool = True):
     lib.lbm_fs_step.argtypes = [P, I32]
     lib.lbm_fs_forces.argtypes = [P, I32, D, D, D, D]
     lib.lbm_fs_body_state.argtypes = [P, I32, C.POINTER(lbm_fs_body_state_t)]
+    lib.lbm_fs_body_states.argtypes = [P, I32, I32, C.POINTER(lbm_fs_body_state_t)]
     lib.lbm_fs_read_fields.argtypes = [P, C.c_uint32, C.POINTER(C.c_void_p), I32]
     lib.lbm_fs_stats.argtypes = [P, C.POINTER(lbm_fs_stats_t)]
     lib.lbm_fs_sync.argtypes = [P]
@@ -144,6 +146,15 @@ def lbm_fs_body_state(h, body: int) -> dict:
     _check(load().lbm_fs_body_state(h, int(body), C.byref(s)), "lbm_fs_body_state")
     return dict(F=np.array(s.F), T=np.array(s.T), S=s.S, center=np.array(s.center), quat=np.array(s.quat),
                 vel=np.array(s.vel), omega=np.array(s.omega))
+
+
+def lbm_fs_body_states(h, first: int, count: int, out=None):
+    """States of bodies first .. first+count-1 with one synchronisation; out
+    may be a preallocated (lbm_fs_body_state_t * count) array."""
+    if out is None:
+        out = (lbm_fs_body_state_t * count)()
+    _check(load().lbm_fs_body_states(h, int(first), int(count), out), "lbm_fs_body_states")
+    return out
 
 
 def lbm_fs_read_fields(h, mask: int, dst: Sequence[Optional[int]], dst_on_device: bool):
