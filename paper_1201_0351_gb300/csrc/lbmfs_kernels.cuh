@@ -547,9 +547,43 @@ __device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
     d.flags[i] = (uint8_t)((d.flags[i] & CL_MASK) | (nb ? NB_OBST : 0));
 }
 
+// neighbour-obstacle bits of the cells x0 <= x < x1 (grid (x-tiles, ny, nz))
 __global__ void k_nb_all(Dev d) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.N; i += (long long)gridDim.x * blockDim.x)
-        nb_refresh(d, i);
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= d.nx) return;
+    long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+    bool nb = false;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        int c = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
+        nb = nb || c == CL_O || c == CL_WALL;
+    }
+    d.flags[i] = (uint8_t)((d.flags[i] & CL_MASK) | (nb ? NB_OBST : 0));
+}
+
+// the same over the cells around body bi (its range widened by one cell)
+__global__ void k_nb_body(Dev d, int bi) {
+    const Body &b = d.bodies[bi];
+    int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, b.lo[2] - 1}, hi[3] = {b.hi[0] + 1, b.hi[1] + 1, b.hi[2] + 1};
+    int n3[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        if (!(d.periodic & (1u << k))) {
+            lo[k] = lo[k] < 0 ? 0 : lo[k];
+            hi[k] = hi[k] > n3[k] ? n3[k] : hi[k];
+        } else if (hi[k] - lo[k] > n3[k]) {
+            hi[k] = lo[k] + n3[k];
+        }
+    }
+    for (int zz = lo[2] + (int)blockIdx.x; zz < hi[2]; zz += gridDim.x) {
+        int z = zz < 0 ? zz + d.nz : (zz >= d.nz ? zz - d.nz : zz);
+        for (int yy = lo[1] + (int)threadIdx.y; yy < hi[1]; yy += blockDim.y) {
+            int y = yy < 0 ? yy + d.ny : (yy >= d.ny ? yy - d.ny : yy);
+            for (int xx = lo[0] + (int)threadIdx.x; xx < hi[0]; xx += blockDim.x) {
+                int x = xx < 0 ? xx + d.nx : (xx >= d.nx ? xx - d.nx : xx);
+                nb_refresh(d, x + (long long)d.nx * (y + (long long)d.ny * z));
+            }
+        }
+    }
 }
 
 // cells whose obstacle status changed this step (covered, uncovered): refresh
@@ -747,7 +781,7 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
 // one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
 // consecutive z (amortises the launch of blocks that meet only gas)
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid(Dev d) {
+__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(Dev d) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     int z0 = blockIdx.z * LBMFS_BULK_ZB;
@@ -1507,12 +1541,12 @@ template <int S> struct Launch {
                            cudaStream_t st) {
         unsigned blocks = (unsigned)((d.N + 255) / 256);
         k_init<S><<<blocks, 256, 0, st>>>(d, flags, fill, rho, vel);
-        k_nb_all<<<LIST_BLOCKS * 4, 256, 0, st>>>(d);
+        k_nb_all<<<dim3((d.nx + 127) / 128, d.ny, d.nz), 128, 0, st>>>(d);
     }
     static void body_prepare(const Dev &d, int b, cudaStream_t st) { k_body_prepare<<<1, 32, 0, st>>>(d, b); }
     static void map_body(const Dev &d, int b, int book, cudaStream_t st) {
         k_map_body<S><<<FORCE_BLOCKS, 256, 0, st>>>(d, b, book);
-        k_nb_all<<<LIST_BLOCKS * 4, 256, 0, st>>>(d);
+        k_nb_body<<<FORCE_BLOCKS, dim3(32, 8), 0, st>>>(d, b);
     }
     static void liquid_mass(const Dev &d, cudaStream_t st) {
         k_mass_partial<S><<<LIST_BLOCKS, 256, 0, st>>>(d);
