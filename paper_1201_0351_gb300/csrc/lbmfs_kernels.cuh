@@ -125,10 +125,18 @@ template <> struct Sto<1> {
 #pragma unroll
         for (int q = 0; q < Q; ++q) st(g, q, i, N, (float)(f[q] - wd(q)));
     }
-    // store deviations d_q; drho = collision density - 1 (unused for float)
-    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, float) {
+    // store the collided deviations dv; the rest population is replaced by
+    // dp_0 + sum_{q>=1} (dp_q - dv_q) (equal to dv_0 in exact arithmetic) so
+    // that the stored cell sum equals the streamed-in sum of dp up to one
+    // rounding of a small number: no mass drift from float rounding
+    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, const float *dp) {
+        float rest = 0.0f;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) st(g, q, i, N, dv[q]);
+        for (int q = 1; q < Q; ++q) {
+            st(g, q, i, N, dv[q]);
+            rest += dp[q] - dv[q];
+        }
+        st(g, 0, i, N, dp[0] + rest);
     }
     static size_t bytes(long long N) { return (size_t)N * Q * sizeof(float); }
 };
@@ -148,28 +156,25 @@ template <> struct Sto<2> {
         return wd(q) + (double)ld(g, q, i, N);
     }
     // d*_q for q >= 1 rounded to half; the rest population takes
-    // (rho - 1) - sum_{q>=1} dequant(h_q) so that the stored sum is rho
-    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, float drho) {
+    // dp_0 + sum_{q>=1} (dp_q - dequant(h_q)) so that the stored cell sum
+    // equals the streamed-in sum of dp (the collision density) up to one
+    // rounding of a small number
+    static __device__ __forceinline__ void st_dev(void *g, long long i, long long N, const float *dv, const float *dp) {
         __half *h = const_cast<__half *>(hp(g, N));
-        float rest = drho;
+        float rest = 0.0f;
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
             __half hq = __float2half_rn(dv[q] * F16_SCALE);
             pop_st(h + ((long long)(q - 1) * N + i), hq);
-            rest -= __half2float(hq) * F16_INV_SCALE;
+            rest += dp[q] - __half2float(hq) * F16_INV_SCALE;
         }
-        pop_st(reinterpret_cast<float *>(g) + i, rest);
+        pop_st(reinterpret_cast<float *>(g) + i, dp[0] + rest);
     }
     static __device__ __forceinline__ void st_cell(void *g, long long i, long long N, const double *f) {
-        double drho = 0.0;
         float dv[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            double d = f[q] - wd(q);
-            drho += d;
-            dv[q] = (float)d;
-        }
-        st_dev(g, i, N, dv, (float)drho);
+        for (int q = 0; q < Q; ++q) dv[q] = (float)(f[q] - wd(q));
+        st_dev(g, i, N, dv, dv);
     }
     static size_t bytes(long long N) { return (size_t)N * (sizeof(float) + (Q - 1) * sizeof(__half)); }
 };
@@ -831,7 +836,7 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     } else {
         float dn[Q], rho;
         float dr = collide_f(d, fp, dn, rho);
-        P::st_dev(d.fdst, i, N, dn, dr);
+        P::st_dev(d.fdst, i, N, dn, fp);
         if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
     }
 }
@@ -1008,7 +1013,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
             m_new = d.m[i] + (double)dm;
             float dn[Q], rho;
             float dr = collide_f(d, fp, dn, rho);
-            P::st_dev(d.fdst, i, N, dn, dr);
+            P::st_dev(d.fdst, i, N, dn, fp);
             float drs = 0.0f;
 #pragma unroll
             for (int q = 0; q < Q; ++q) drs += P::ld(d.fdst, q, i, N);

@@ -144,3 +144,20 @@ def test_mass_ledger_identity_f64():
     resid = s["liquid_mass"] - s["mass0"] - (s["uncovered"] - s["covered"] - s["lost_excess"] + s["wall_source"])
     assert abs(resid) <= 1e-12 * s["mass0"], s
     assert s["covered"] > 0 and abs(s["wall_source"]) > 1e-3
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_reduced_precision_mass_drift(storage):
+    """Total liquid mass drift below 1e-9 per 10^4 steps (closed tank with the
+    fixed box: no moving-wall source, so M - M0 - ledger measures rounding
+    drift alone)."""
+    from paper_1201_0351_gb300 import lbm_fs
+    steps = 400
+    sim = lbm_fs.Simulation(I.closed_tank_32(), storage=storage)
+    sim.step(steps)
+    s = sim.stats()
+    sim.close()
+    resid = s["liquid_mass"] - s["mass0"] - (s["uncovered"] - s["covered"] - s["lost_excess"] + s["wall_source"])
+    drift_per_1e4 = abs(resid) / s["mass0"] * (1e4 / steps)
+    print(storage, "drift per 1e4 steps", drift_per_1e4)
+    assert drift_per_1e4 < 1e-9, s
