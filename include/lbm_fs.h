@@ -49,7 +49,7 @@ typedef enum {
     LBM_FS_ECUDA = -3,     /* a CUDA runtime call failed */
     LBM_FS_ESTATE = -4,    /* call not valid in the handle's state */
     LBM_FS_EUNSTABLE = -5, /* non-finite density, or liquid touching gas */
-    LBM_FS_ETIMEOUT = -6,  /* reserved: a bounded device wait gave up */
+    LBM_FS_ETIMEOUT = -6,  /* a bounded device wait (staged row copies) gave up */
     LBM_FS_EOVERFLOW = -7  /* a device worklist overflowed */
 } lbm_fs_status;
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -91,6 +92,7 @@ lbm_fs_status read_status(lbm_fs *h) {
     CK(cudaStreamSynchronize(h->st));
     CK(cudaMemcpy(&st, h->d[0].status, sizeof st, cudaMemcpyDeviceToHost));
     if (st & ST_OVERFLOW) return fail(LBM_FS_EOVERFLOW, "a device worklist overflowed%s");
+    if (st & ST_TIMEOUT) return fail(LBM_FS_ETIMEOUT, "a bounded wait for staged rows gave up%s");
     if (st & ST_NONFINITE) return fail(LBM_FS_EUNSTABLE, "non-finite or non-positive density in a fluid cell%s");
     if (st & ST_LIQUID_GAS) return fail(LBM_FS_EUNSTABLE, "a liquid cell touched a gas cell (open interface layer)%s");
     return LBM_FS_OK;
@@ -198,12 +200,20 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.rho_g = p->rho_gas;
     d.eps = p->eps;
     d.cap = (uint32_t)N;
+    // row segments are 16-byte aligned when nx is a multiple of 16 / element size
+    d.tma = (p->storage == LBM_FS_F32 && p->nx % 4 == 0) || (p->storage == LBM_FS_F16S && p->nx % 8 == 0);
+    if (getenv("LBMFS_NO_TMA")) d.tma = 0;
     size_t fb = storage_bytes(p->storage, N);
     size_t nb4 = ((size_t)N + 3) & ~(size_t)3;
     d.flags = (uint8_t *)h->alloc(nb4);
     d.bid = (uint8_t *)h->alloc(nb4);
     d.cmark = (uint8_t *)h->alloc(nb4);
-    void *fA = h->alloc(fb), *fB = h->alloc(fb);
+    // population grids with guard bands: the staged bulk kernel reads a
+    // 16-byte halo around each row segment, which at the grid's first and
+    // last rows reaches past the population array
+    void *fA = h->alloc(fb + 2 * GRID_GUARD), *fB = h->alloc(fb + 2 * GRID_GUARD);
+    if (fA) fA = (char *)fA + GRID_GUARD;
+    if (fB) fB = (char *)fB + GRID_GUARD;
     double *pA = (double *)h->alloc(N * 8), *pB = (double *)h->alloc(N * 8);
     d.m = (double *)h->alloc(N * 8);
     for (int k = 0; k < WL_COUNT; ++k) d.list[k] = (uint32_t *)h->alloc(N * 4);
@@ -226,8 +236,8 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
         if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call));   \
     } while (0)
     CKB(cudaMemsetAsync(d.cmark, 0, nb4, st));
-    CKB(cudaMemsetAsync(fA, 0, fb, st));
-    CKB(cudaMemsetAsync(fB, 0, fb, st));
+    CKB(cudaMemsetAsync((char *)fA - GRID_GUARD, 0, fb + 2 * GRID_GUARD, st));
+    CKB(cudaMemsetAsync((char *)fB - GRID_GUARD, 0, fb + 2 * GRID_GUARD, st));
     CKB(cudaMemsetAsync(pA, 0, N * 8, st));
     CKB(cudaMemsetAsync(pB, 0, N * 8, st));
     CKB(cudaMemsetAsync(d.m, 0, N * 8, st));

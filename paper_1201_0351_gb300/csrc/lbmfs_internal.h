@@ -12,6 +12,10 @@ constexpr int FORCE_BLOCKS = 64;   // blocks per body in the force / remap kerne
 constexpr int LIST_BLOCKS = 304;   // 2 x 152 SMs: grid of the worklist kernels
 constexpr int LIST_THREADS = 256;
 constexpr int REMAP_THREADS = 512;
+// bytes before / after each population grid: the staged bulk kernel copies
+// whole 128-cell row segments plus a 16-byte halo, which for the last x tile of
+// the grid's last row reaches up to (128 + 8) elements past the array end
+constexpr int GRID_GUARD = 1024;
 #ifndef LBMFS_BULK_THREADS
 #define LBMFS_BULK_THREADS 128
 #endif
@@ -25,7 +29,7 @@ enum : uint8_t {
     MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_PEND = 32, MK_FRESH = 64
 };
 // sticky device status bits
-enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
+enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEOUT = 8 };
 
 // worklists
 enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_COUNT };
@@ -62,6 +66,7 @@ struct Dev {
     uint8_t *rdec;  // remap scratch: decision per pending item
     double *rrho, *rphi;
     double *red;    // reduction scratch
+    int tma;        // bulk kernel stages rows with TMA bulk copies (row alignment holds)
 };
 
 struct KernelSet {

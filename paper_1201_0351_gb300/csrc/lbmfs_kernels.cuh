@@ -795,6 +795,44 @@ __global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_
 }
 
 template <int S>
+__device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *fp, long long i) {
+    using P = Sto<S>;
+    if constexpr (!P::shifted) {
+        double fn[Q];
+        collide_d(d, fp, fn);
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            P::st(d.fdst, q, i, d.N, fn[q]);
+            r += fn[q];
+        }
+        if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
+    } else {
+        float dn[Q], rho;
+        collide_f(d, fp, dn, rho);
+        P::st_dev(d.fdst, i, d.N, dn, fp);
+        if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+    }
+}
+
+// liquid cell with an obstacle or wall neighbour, or on a periodic seam:
+// per-direction source classes, bounce-back where the source is solid
+template <int S>
+__device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
+    using P = Sto<S>;
+    typename P::R fp[Q];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+        int ns = cls(d, si);
+        if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, d.N);
+        else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
+    }
+    fp[0] = P::ld(d.fsrc, 0, i, d.N);
+    collide_store<S>(d, fp, i);
+}
+
+template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     using P = Sto<S>;
     using R = typename P::R;
@@ -803,41 +841,178 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     int c = in ? (int)d.flags[i] : 0;
     wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
     if ((c & CL_MASK) != CL_L) return;
-    const long long N = d.N;
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
-    const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
-    R fp[Q];
     if (c == CL_L && interior) {
         // no obstacle or wall in the neighbourhood and a liquid cell never
         // touches gas: plain pull from the 18 neighbours, no flag loads
+        const long long N = d.N;
+        const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
+        R fp[Q];
 #pragma unroll
         for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
         fp[0] = P::ld(d.fsrc, 0, i, N);
+        collide_store<S>(d, fp, i);
     } else {
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            int ns = cls(d, si);
-            if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, N);
-            else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
-        }
-        fp[0] = P::ld(d.fsrc, 0, i, N);
+        liquid_cell_general<S>(d, x, y, z, i);
     }
-    if constexpr (!P::shifted) {
-        double fn[Q];
-        collide_d(d, fp, fn);
-        double r = 0.0;
+}
+
+// ------------------------------------------------ staged bulk kernel (TMA)
+//
+// One block owns a row segment of BULK_THREADS cells at (y, z) for
+// LBMFS_BULK_ZB consecutive z.  For every z it needs, per direction q, the
+// source row (y - c_qy, z - c_qz) of plane q shifted by -c_qx: thread 0 stages
+// those 19 rows (each widened by a 16-byte halo on both sides so that every
+// copy starts 16-byte aligned) into shared memory with 1-D bulk copies that
+// complete on an mbarrier, one z ahead of the rows being computed (double
+// buffer).  Rows whose segment holds no interior liquid cell (gas, or the
+// grid's boundary layers) are not staged.  Cells that need more than a plain
+// pull (obstacle or wall neighbours) use the global-memory path.
+
+template <int S> struct Stage;
+template <> struct Stage<1> {  // float planes, halo 4 elements
+    static constexpr int H = 4;
+    static constexpr int ROW = BULK_THREADS + 2 * H;  // elements per staged row
+    static constexpr int BYTES = Q * ROW * 4;
+    static __device__ __forceinline__ const char *src(const Dev &d, int q, long long e) {
+        return reinterpret_cast<const char *>(reinterpret_cast<const float *>(d.fsrc) + (long long)q * d.N + e);
+    }
+    static __device__ __forceinline__ int row_bytes(int) { return ROW * 4; }
+    static __device__ __forceinline__ int row_off(int q) { return q * ROW * 4; }
+    static __device__ __forceinline__ float get(const char *stage, int q, int k) {
+        return reinterpret_cast<const float *>(stage + row_off(q))[k];
+    }
+};
+template <> struct Stage<2> {  // q = 0 float (halo 4), q >= 1 half (halo 8)
+    static constexpr int H0 = 4, H = 8;
+    static constexpr int ROW0 = BULK_THREADS + 2 * H0, ROW = BULK_THREADS + 2 * H;
+    static constexpr int BYTES = ROW0 * 4 + (Q - 1) * ROW * 2;
+    static __device__ __forceinline__ const char *src(const Dev &d, int q, long long e) {
+        if (q == 0) return reinterpret_cast<const char *>(reinterpret_cast<const float *>(d.fsrc) + e);
+        const __half *hb = reinterpret_cast<const __half *>(reinterpret_cast<const float *>(d.fsrc) + d.N);
+        return reinterpret_cast<const char *>(hb + (long long)(q - 1) * d.N + e);
+    }
+    static __device__ __forceinline__ int row_bytes(int q) { return q == 0 ? ROW0 * 4 : ROW * 2; }
+    static __device__ __forceinline__ int row_off(int q) { return q == 0 ? 0 : ROW0 * 4 + (q - 1) * ROW * 2; }
+    static __device__ __forceinline__ float get(const char *stage, int q, int k) {
+        if (q == 0) return reinterpret_cast<const float *>(stage)[k];
+        return __half2float(reinterpret_cast<const __half *>(stage + row_off(q))[k]) * F16_INV_SCALE;
+    }
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// order earlier generic-proxy accesses to shared memory before the async-proxy
+// (bulk copy) writes that follow
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: gives up after ~2^22 polls (each try_wait also suspends for a
+// hardware-chosen interval), far beyond any copy latency
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int S>
+__device__ __forceinline__ void stage_row(const Dev &d, char *stage, uint64_t *bar, int x0, int y, int z) {
+    using G = Stage<S>;
+    fence_async_shared();
+    mbar_expect_tx(bar, G::BYTES);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            P::st(d.fdst, q, i, N, fn[q]);
-            r += fn[q];
+    for (int q = 0; q < Q; ++q) {
+        // the copy starts 16-byte aligned at x0 - h for every direction; the
+        // x shift -c_qx is applied when the row is read
+        int h = (S == 2 && q > 0) ? Stage<2>::H : 4;
+        long long e = (long long)d.nx * ((y - cy(q)) + (long long)d.ny * (z - cz(q))) + x0 - h;
+        bulk_g2s(stage + G::row_off(q), G::src(d, q, e), G::row_bytes(q), bar);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_tma(Dev d) {
+    using P = Sto<S>;
+    using G = Stage<S>;
+    extern __shared__ __align__(128) char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // two mbarriers
+    char *buf0 = smem + 128;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * BULK_THREADS, x = x0 + tid, y = blockIdx.y;
+    const int z0 = blockIdx.z * LBMFS_BULK_ZB, z1 = min(z0 + LBMFS_BULK_ZB, d.nz);
+    const bool in = x < d.nx;
+    const bool xin = x > 0 && x < d.nx - 1;
+    const bool yin = y > 0 && y < d.ny - 1;
+    bool failed = false;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned phase[2] = {0u, 0u};
+    auto flag_at = [&](int z) -> int {
+        return (in && z < z1) ? (int)d.flags[x + (long long)d.nx * (y + (long long)d.ny * z)] : 0;
+    };
+    auto fast = [&](int fl, int z) -> bool { return fl == CL_L && xin && yin && z > 0 && z < d.nz - 1; };
+    int fl_cur = flag_at(z0);
+    bool staged_cur = __syncthreads_or(fast(fl_cur, z0)) != 0;
+    if (staged_cur && tid == 0) stage_row<S>(d, buf0, &bar[0], x0, y, z0);
+    int fl_next = flag_at(z0 + 1);
+    for (int z = z0; z < z1; ++z) {
+        const int b = (z - z0) & 1;
+        char *stage = buf0 + b * G::BYTES;
+        // every thread is done with the other buffer (previous row) here
+        bool staged_next = __syncthreads_or(z + 1 < z1 && fast(fl_next, z + 1)) != 0;
+        if (staged_next && tid == 0) stage_row<S>(d, buf0 + (b ^ 1) * G::BYTES, &bar[b ^ 1], x0, y, z + 1);
+        int fl_after = flag_at(z + 2);
+        const long long i = (long long)(in ? x : 0) + (long long)d.nx * (y + (long long)d.ny * z);
+        const int c = fl_cur;
+        wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
+        if (staged_cur) {
+            // every thread keeps stepping through the block barriers even if
+            // its wait gives up; the outcome is settled after the loop
+            if (!mbar_wait(&bar[b], phase[b])) failed = true;
+            phase[b] ^= 1u;
         }
-        if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
-    } else {
-        float dn[Q], rho;
-        float dr = collide_f(d, fp, dn, rho);
-        P::st_dev(d.fdst, i, N, dn, fp);
-        if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+        if (fast(c, z)) {
+            float fp[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) fp[q] = G::get(stage, q, tid + ((S == 2 && q > 0) ? Stage<2>::H : 4) - cx(q));
+            float dn[Q], rho;
+            collide_f(d, fp, dn, rho);
+            P::st_dev(d.fdst, i, d.N, dn, fp);
+            if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+        } else if ((c & CL_MASK) == CL_L) {
+            liquid_cell_general<S>(d, x, y, z, i);
+        }
+        fl_cur = fl_next;
+        fl_next = fl_after;
+        staged_cur = staged_next;
+    }
+    if (__syncthreads_or(failed)) {
+        // a staged copy did not complete in time: report it; every staged row
+        // has had its (bounded) wait above, so no copy is left unawaited
+        if (tid == 0) atomicOr(d.status, ST_TIMEOUT);
     }
 }
 
@@ -1577,8 +1752,15 @@ template <int S> struct Launch {
         mark();
         if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), dim3(32, 8), 0, st>>>(d);
         mark();
-        k_liquid<S><<<dim3((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB),
-                      BULK_THREADS, 0, st>>>(d);
+        {
+            dim3 grid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
+            if constexpr (S != 0) {
+                if (d.tma) k_liquid_tma<S><<<grid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
+                else k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
+            } else {
+                k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
+            }
+        }
         mark();
         k_interface<S><<<LIST_BLOCKS * 2, 128, 0, st>>>(d);
         mark();

@@ -161,3 +161,22 @@ def test_reduced_precision_mass_drift(storage):
     drift_per_1e4 = abs(resid) / s["mass0"] * (1e4 / steps)
     print(storage, "drift per 1e4 steps", drift_per_1e4)
     assert drift_per_1e4 < 1e-9, s
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_staged_bulk_kernel_matches_plain_kernel(storage, monkeypatch):
+    """The TMA-staged bulk kernel reads the same populations as the plain one
+    (through shared memory instead of direct loads): results are bit-identical."""
+    from paper_1201_0351_gb300 import lbm_fs
+    sc = I.random_box_scene(40, 30, 22, seed=5, nboxes=3, speed=0.02)
+    out = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("LBMFS_NO_TMA", "1")
+        sim = lbm_fs.Simulation(sc, storage=storage)
+        sim.step(40)
+        out.append((sim.fields(want_f=True), sim.body(0)))
+        sim.close()
+    assert np.array_equal(out[0][0]["flags"], out[1][0]["flags"])
+    assert np.array_equal(out[0][0]["f"], out[1][0]["f"])
+    assert np.array_equal(out[0][1]["F"], out[1][1]["F"])
