@@ -139,6 +139,11 @@ template <> struct Sto<1> {
         st(g, 0, i, N, dp[0] + rest);
     }
     static size_t bytes(long long N) { return (size_t)N * Q * sizeof(float); }
+    // store one deviation, return the value as stored
+    static __device__ __forceinline__ float st_one(void *g, int q, long long i, long long N, float v) {
+        st(g, q, i, N, v);
+        return v;
+    }
 };
 
 template <> struct Sto<2> {
@@ -177,6 +182,15 @@ template <> struct Sto<2> {
         st_dev(g, i, N, dv, dv);
     }
     static size_t bytes(long long N) { return (size_t)N * (sizeof(float) + (Q - 1) * sizeof(__half)); }
+    static __device__ __forceinline__ float st_one(void *g, int q, long long i, long long N, float v) {
+        if (q == 0) {
+            pop_st(reinterpret_cast<float *>(g) + i, v);
+            return v;
+        }
+        __half hq = __float2half_rn(v * F16_SCALE);
+        pop_st(const_cast<__half *>(hp(g, N)) + ((long long)(q - 1) * N + i), hq);
+        return __half2float(hq) * F16_INV_SCALE;
+    }
 };
 
 // ---------------------------------------------------------------- helpers
@@ -426,6 +440,45 @@ __device__ __forceinline__ float collide_f(const Dev &d, const float *dp, float 
     }
     rho_out = rho;
     return dr;
+}
+
+// Collision fused with the store for the float storages: each collided
+// deviation is stored as soon as it is computed, and the rest population is
+// stored as dp_0 + sum_{q>=1} (dp_q - stored_q): equal to the collided rest
+// population in exact arithmetic, it makes the stored cell sum equal the
+// streamed-in sum up to one rounding (no mass drift from float rounding).
+// Returns the collision density.
+template <class Store>
+__device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, Store store) {
+    float dr = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dr += dp[q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (cx(q)) j0 += cx(q) * dp[q];
+        if (cy(q)) j1 += cy(q) * dp[q];
+        if (cz(q)) j2 += cz(q) * dp[q];
+    }
+    float rho = 1.0f + dr;
+    float inv = 1.0f / rho;
+    float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
+    float usq = ux * ux + uy * uy + uz * uz;
+    float om = (float)d.omega;
+    float ax = (float)d.a[0], ay = (float)d.a[1], az = (float)d.a[2];
+    float ua = ux * ax + uy * ay + uz * az;
+    float rest = 0.0f;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
+        float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
+        float deq = wf(q) * (dr + s + dr * s);
+        float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
+        float fq = wf(q) * rho * (3.0f * (ca - ua) + 9.0f * cu * ca);
+        float dn = dp[q] - om * (dp[q] - deq) + fq;
+        rest += dp[q] - store(q, dn);
+    }
+    store(0, dp[0] + rest);
+    return rho;
 }
 
 // f_eq(rho_g, u) - w as float deviation
@@ -791,6 +844,7 @@ __global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_
     int y = blockIdx.y;
     int z0 = blockIdx.z * LBMFS_BULK_ZB;
     int z1 = min(z0 + LBMFS_BULK_ZB, d.nz);
+#pragma unroll 1
     for (int z = z0; z < z1; ++z) liquid_cell<S>(d, x, y, z);
 }
 
@@ -808,19 +862,20 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         }
         if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
     } else {
-        float dn[Q], rho;
-        collide_f(d, fp, dn, rho);
-        P::st_dev(d.fdst, i, d.N, dn, fp);
+        void *g = d.fdst;
+        const long long N = d.N;
+        float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st_one(g, q, i, N, v); });
         if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
     }
 }
 
-// liquid cell with an obstacle or wall neighbour, or on a periodic seam:
-// per-direction source classes, bounce-back where the source is solid
+// populations arriving at a liquid cell with an obstacle or wall neighbour, or
+// on a periodic seam: per-direction source classes, bounce-back where the
+// source is solid
 template <int S>
-__device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
+__device__ __forceinline__ void gather_general(const Dev &d, int x, int y, int z, long long i,
+                                               typename Sto<S>::R *fp) {
     using P = Sto<S>;
-    typename P::R fp[Q];
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
@@ -829,6 +884,12 @@ __device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, 
         else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
     }
     fp[0] = P::ld(d.fsrc, 0, i, d.N);
+}
+
+template <int S>
+__device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
+    typename Sto<S>::R fp[Q];
+    gather_general<S>(d, x, y, z, i, fp);
     collide_store<S>(d, fp, i);
 }
 
@@ -842,19 +903,19 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
     if ((c & CL_MASK) != CL_L) return;
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+    R fp[Q];
     if (c == CL_L && interior) {
         // no obstacle or wall in the neighbourhood and a liquid cell never
         // touches gas: plain pull from the 18 neighbours, no flag loads
         const long long N = d.N;
         const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
-        R fp[Q];
 #pragma unroll
         for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
         fp[0] = P::ld(d.fsrc, 0, i, N);
-        collide_store<S>(d, fp, i);
     } else {
-        liquid_cell_general<S>(d, x, y, z, i);
+        gather_general<S>(d, x, y, z, i, fp);
     }
+    collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
 }
 
 // ------------------------------------------------ staged bulk kernel (TMA)
@@ -998,9 +1059,9 @@ __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_tma(De
             float fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fp[q] = G::get(stage, q, tid + ((S == 2 && q > 0) ? Stage<2>::H : 4) - cx(q));
-            float dn[Q], rho;
-            collide_f(d, fp, dn, rho);
-            P::st_dev(d.fdst, i, d.N, dn, fp);
+            void *g = d.fdst;
+            const long long N = d.N;
+            float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st_one(g, q, i, N, v); });
             if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
         } else if ((c & CL_MASK) == CL_L) {
             liquid_cell_general<S>(d, x, y, z, i);
@@ -1186,12 +1247,13 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
                 }
             }
             m_new = d.m[i] + (double)dm;
-            float dn[Q], rho;
-            float dr = collide_f(d, fp, dn, rho);
-            P::st_dev(d.fdst, i, N, dn, fp);
+            void *g = d.fdst;
             float drs = 0.0f;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) drs += P::ld(d.fdst, q, i, N);
+            float rho = collide_store_f(d, fp, [&](int q, float v) {
+                float st = P::st_one(g, q, i, N, v);
+                drs += st;
+                return st;
+            });
             double r = 1.0 + (double)drs;
             double phin = m_new / r;
             d.m[i] = m_new;

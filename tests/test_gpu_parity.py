@@ -170,9 +170,11 @@ def test_staged_bulk_kernel_matches_plain_kernel(storage, monkeypatch):
     from paper_1201_0351_gb300 import lbm_fs
     sc = I.random_box_scene(40, 30, 22, seed=5, nboxes=3, speed=0.02)
     out = []
-    for no_tma in (False, True):
-        if no_tma:
-            monkeypatch.setenv("LBMFS_NO_TMA", "1")
+    for tma in (True, False):
+        if tma:
+            monkeypatch.setenv("LBMFS_TMA", "1")
+        else:
+            monkeypatch.delenv("LBMFS_TMA", raising=False)
         sim = lbm_fs.Simulation(sc, storage=storage)
         sim.step(40)
         out.append((sim.fields(want_f=True), sim.body(0)))
