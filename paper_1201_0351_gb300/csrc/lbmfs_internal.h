@@ -66,8 +66,12 @@ struct Dev {
     uint8_t *rdec;  // remap scratch: decision per pending item
     double *rrho, *rphi;
     double *red;    // reduction scratch
-    int tma;        // bulk kernel stages rows with TMA bulk copies (row alignment holds)
+    int bulk;       // bulk-kernel variant for the float storages (BULK_*)
 };
+
+// bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,
+// TMA-staged rows (needs 16-byte aligned rows)
+enum { BULK_PLAIN = 0, BULK_PIPE = 1, BULK_TMA = 2 };
 
 struct KernelSet {
     void (*init_cells)(const Dev &, const uint8_t *flags, const double *fill, const double *rho, const double *vel,

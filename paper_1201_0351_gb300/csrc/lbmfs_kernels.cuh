@@ -69,6 +69,9 @@ constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2
 #ifndef LBMFS_BULK_ZB
 #define LBMFS_BULK_ZB 4    // z-planes per bulk-kernel block
 #endif
+#ifndef LBMFS_BULK_PIPE_ZB
+#define LBMFS_BULK_PIPE_ZB 16  // z-planes per block of the software-pipelined bulk kernel
+#endif
 #ifndef LBMFS_ST_CS
 #define LBMFS_ST_CS 0      // population stores with the evict-first (streaming) hint
 #endif
@@ -194,6 +197,11 @@ template <> struct Sto<2> {
 };
 
 // ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// order earlier generic-proxy accesses to shared memory before the async-proxy
+// (bulk copy) writes that follow
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ long long nbr(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
     int px = x + dx, py = y + dy, pz = z + dz;
@@ -918,6 +926,100 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
 }
 
+// ---------------------------------------- software-pipelined bulk kernel
+//
+// Each thread copies the 19 populations its cell will pull at the next z into
+// private shared-memory slots with cp.async (4-byte copies, no register held
+// while in flight) before it collides the cell at the current z: two planes of
+// loads in flight per thread.  A thread reads only its own slots, so no block
+// barrier is needed; cp.async.wait_group orders the copies with the reads.
+// FP16 storage copies the aligned 4-byte word holding the wanted half.
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int S> struct Pipe;
+template <> struct Pipe<1> {
+    static __device__ __forceinline__ const void *src(const Dev &d, int q, long long e) {
+        return reinterpret_cast<const float *>(d.fsrc) + (long long)q * d.N + e;
+    }
+    static __device__ __forceinline__ float get(const uint32_t *slot, int q, long long, long long) {
+        return __uint_as_float(slot[q * BULK_THREADS]);
+    }
+};
+template <> struct Pipe<2> {
+    static __device__ __forceinline__ const void *src(const Dev &d, int q, long long e) {
+        if (q == 0) return reinterpret_cast<const float *>(d.fsrc) + e;
+        const __half *h = reinterpret_cast<const __half *>(reinterpret_cast<const float *>(d.fsrc) + d.N) +
+                          (long long)(q - 1) * d.N + e;
+        return reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(h) & ~(uintptr_t)3);
+    }
+    static __device__ __forceinline__ float get(const uint32_t *slot, int q, long long e, long long N) {
+        uint32_t w = slot[q * BULK_THREADS];
+        if (q == 0) return __uint_as_float(w);
+        // the half planes start 4-byte aligned; the parity of the half's index
+        // counted from there picks the half within the copied word
+        long long h = (long long)(q - 1) * N + e;
+        unsigned short hb = (unsigned short)((h & 1) ? (w >> 16) : (w & 0xffffu));
+        return __half2float(__ushort_as_half(hb)) * F16_INV_SCALE;
+    }
+};
+
+template <int S>
+__global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_pipe(Dev d) {
+    using P = Sto<S>;
+    __shared__ uint32_t slots[2][Q][BULK_THREADS];
+    const int tid = threadIdx.x;
+    const int x = blockIdx.x * BULK_THREADS + tid, y = blockIdx.y;
+    const int z0 = blockIdx.z * LBMFS_BULK_PIPE_ZB, z1 = min(z0 + LBMFS_BULK_PIPE_ZB, d.nz);
+    const bool in = x < d.nx;
+    const bool xyin = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1;
+    const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
+    const long long irow = (long long)(in ? x : 0) + (long long)d.nx * y;
+    auto flag_at = [&](int z) -> int { return (in && z < z1) ? (int)d.flags[irow + sz * z] : 0; };
+    auto fast = [&](int fl, int z) -> bool { return fl == CL_L && xyin && z > 0 && z < d.nz - 1; };
+    auto issue = [&](int z, int b) {
+        const long long i = irow + sz * z;
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            cp_async4(&slots[b][q][tid], Pipe<S>::src(d, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz)));
+    };
+    int fl_cur = flag_at(z0);
+    bool fast_cur = fast(fl_cur, z0);
+    if (fast_cur) issue(z0, 0);
+    cp_async_commit();
+    int fl_next = flag_at(z0 + 1);
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        const int b = (z - z0) & 1;
+        const bool fast_next = z + 1 < z1 && fast(fl_next, z + 1);
+        if (fast_next) issue(z + 1, b ^ 1);
+        cp_async_commit();
+        const int fl_after = flag_at(z + 2);
+        const long long i = irow + sz * z;
+        wl_append(d, (fl_cur & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
+        if (fast_cur) {
+            cp_async_wait<1>();
+            float fp[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                fp[q] = Pipe<S>::get(&slots[b][0][tid], q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), d.N);
+            collide_store<S>(d, fp, i);
+        } else if ((fl_cur & CL_MASK) == CL_L) {
+            liquid_cell_general<S>(d, x, y, z, i);
+        }
+        fl_cur = fl_next;
+        fl_next = fl_after;
+        fast_cur = fast_next;
+    }
+    cp_async_wait<0>();
+}
+
 // ------------------------------------------------ staged bulk kernel (TMA)
 //
 // One block owns a row segment of BULK_THREADS cells at (y, z) for
@@ -961,10 +1063,6 @@ template <> struct Stage<2> {  // q = 0 float (halo 4), q >= 1 half (halo 8)
     }
 };
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-// order earlier generic-proxy accesses to shared memory before the async-proxy
-// (bulk copy) writes that follow
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -1817,7 +1915,9 @@ template <int S> struct Launch {
         {
             dim3 grid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
             if constexpr (S != 0) {
-                if (d.tma) k_liquid_tma<S><<<grid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
+                dim3 pgrid(grid.x, grid.y, (d.nz + LBMFS_BULK_PIPE_ZB - 1) / LBMFS_BULK_PIPE_ZB);
+                if (d.bulk == BULK_TMA) k_liquid_tma<S><<<grid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
+                else if (d.bulk == BULK_PIPE) k_liquid_pipe<S><<<pgrid, BULK_THREADS, 0, st>>>(d);
                 else k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
             } else {
                 k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
