@@ -959,36 +959,26 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     if ((c & CL_MASK) != CL_L) return;
     const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
     R fp[Q];
-    if constexpr (IDX32) {
-        const int i32 = (int)i;
-        if (c == CL_L && interior) {
-            // no obstacle or wall in the neighbourhood and a liquid cell never
-            // touches gas: plain pull from the 18 neighbours, no flag loads
+    if (c == CL_L && interior) {
+        // no obstacle or wall in the neighbourhood and a liquid cell never
+        // touches gas: plain pull from the 18 neighbours, no flag loads
+        if constexpr (IDX32) {
+            const int i32 = (int)i;
 #pragma unroll
             for (int q = 0; q < Q; ++q) fp[q] = P::ld32(d, q, i32 + d.pull32[q]);
+            collide_store32<S>(d, fp, i32);
+            return;
         } else {
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                int ns = cls(d, si);
-                if (ns == CL_L || ns == CL_I) fp[q] = P::ld32(d, q, (int)si + d.put32[q]);
-                else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
-            }
-            fp[0] = P::ld32(d, 0, i32 + d.put32[0]);
-        }
-        collide_store32<S>(d, fp, i32);  // the kernel's one copy of the collision
-    } else {
-        if (c == CL_L && interior) {
             const long long N = d.N;
             const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
 #pragma unroll
             for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
             fp[0] = P::ld(d.fsrc, 0, i, N);
-        } else {
-            gather_general<S>(d, x, y, z, i, fp);
         }
-        collide_store<S>(d, fp, i);  // the kernel's one copy of the collision
+    } else {
+        gather_general<S>(d, x, y, z, i, fp);
     }
+    collide_store<S>(d, fp, i);  // one copy of the general collision in the kernel
 }
 
 // ---------------------------------------- software-pipelined bulk kernel
