@@ -200,31 +200,18 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.rho_g = p->rho_gas;
     d.eps = p->eps;
     d.cap = (uint32_t)N;
-    d.idx32 = 19 * N < 2147483647ll && getenv("LBMFS_IDX64") == nullptr;
-    {
-        static const int C3[Q][3] = {{0, 0, 0},   {-1, 0, 0}, {1, 0, 0},  {0, 1, 0},  {0, -1, 0},
-                                     {0, 0, 1},   {0, 0, -1}, {-1, 0, 1}, {1, 0, 1},  {0, 1, 1},
-                                     {0, -1, 1},  {-1, 1, 0}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                                     {-1, 0, -1}, {1, 0, -1}, {0, 1, -1}, {0, -1, -1}};
-        for (int q = 0; q < Q; ++q) {
-            long long pull = C3[q][0] + (long long)p->nx * (C3[q][1] + (long long)p->ny * C3[q][2]);
-            long long plane = p->storage == LBM_FS_F16S ? (q == 0 ? 0 : (long long)(q - 1) * N) : (long long)q * N;
-            d.pull32[q] = d.idx32 ? (int)(plane - pull) : 0;
-            d.put32[q] = d.idx32 ? (int)plane : 0;
-        }
-    }
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
-    // bulk-kernel variant (float storages): direct loads by default;
-    // LBMFS_BULK=pipe|tma selects the shared-memory staged variants (both
-    // measured slower on GB300; the TMA one needs rows of 16-byte multiples)
-    d.bulk = BULK_PLAIN;
+    // bulk-kernel variant (float storages): the software-pipelined kernel by
+    // default; LBMFS_BULK=plain|pipe|tma selects another one (the TMA-staged
+    // kernel needs rows of 16-byte multiples and measured slower)
+    d.bulk = BULK_PIPE;
     if (const char *v = getenv("LBMFS_BULK")) {
-        if (!strcmp(v, "pipe")) d.bulk = BULK_PIPE;
+        if (!strcmp(v, "plain")) d.bulk = BULK_PLAIN;
         else if (!strcmp(v, "tma")) d.bulk = BULK_TMA;
     }
     if (d.bulk == BULK_TMA &&
         !((p->storage == LBM_FS_F32 && p->nx % 4 == 0) || (p->storage == LBM_FS_F16S && p->nx % 8 == 0)))
-        d.bulk = BULK_PLAIN;
+        d.bulk = BULK_PIPE;
     size_t fb = storage_bytes(p->storage, N);
     size_t nb4 = ((size_t)N + 3) & ~(size_t)3;
     d.flags = (uint8_t *)h->alloc(nb4);

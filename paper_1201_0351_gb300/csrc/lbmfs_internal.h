@@ -67,13 +67,6 @@ struct Dev {
     double *rrho, *rphi;
     double *red;    // reduction scratch
     int bulk;       // bulk-kernel variant for the float storages (BULK_*)
-    // 32-bit element offsets for grids with 19 N < 2^31: the population pulled
-    // along q by interior cell i sits at element i + pull32[q] of the source
-    // array (plane q of a float / double grid, or of the half planes for
-    // q >= 1 of FP16 storage); its destination at i + put32[q]
-    int idx32;
-    int pull32[Q];
-    int put32[Q];
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,

@@ -110,13 +110,6 @@ template <> struct Sto<0> {
         for (int q = 0; q < Q; ++q) st(g, q, i, N, f[q]);
     }
     static size_t bytes(long long N) { return (size_t)N * Q * sizeof(double); }
-    // 32-bit element index (grids with 19 N < 2^31)
-    static __device__ __forceinline__ double ld32(const Dev &d, int q, int e) {
-        return reinterpret_cast<const double *>(d.fsrc)[e];
-    }
-    static __device__ __forceinline__ void st32(const Dev &d, int q, int e, double v) {
-        pop_st(reinterpret_cast<double *>(d.fdst) + e, v);
-    }
 };
 
 template <> struct Sto<1> {
@@ -149,13 +142,6 @@ template <> struct Sto<1> {
         st(g, 0, i, N, dp[0] + rest);
     }
     static size_t bytes(long long N) { return (size_t)N * Q * sizeof(float); }
-    static __device__ __forceinline__ float ld32(const Dev &d, int q, int e) {
-        return reinterpret_cast<const float *>(d.fsrc)[e];
-    }
-    static __device__ __forceinline__ float st32_one(const Dev &d, int q, int e, float v) {
-        pop_st(reinterpret_cast<float *>(d.fdst) + e, v);
-        return v;
-    }
     // store one deviation, return the value as stored
     static __device__ __forceinline__ float st_one(void *g, int q, long long i, long long N, float v) {
         st(g, q, i, N, v);
@@ -199,20 +185,6 @@ template <> struct Sto<2> {
         st_dev(g, i, N, dv, dv);
     }
     static size_t bytes(long long N) { return (size_t)N * (sizeof(float) + (Q - 1) * sizeof(__half)); }
-    // 32-bit index: q = 0 into the float plane, q >= 1 into the half planes
-    static __device__ __forceinline__ float ld32(const Dev &d, int q, int e) {
-        if (q == 0) return reinterpret_cast<const float *>(d.fsrc)[e];
-        return __half2float(hp(d.fsrc, d.N)[e]) * F16_INV_SCALE;
-    }
-    static __device__ __forceinline__ float st32_one(const Dev &d, int q, int e, float v) {
-        if (q == 0) {
-            pop_st(reinterpret_cast<float *>(d.fdst) + e, v);
-            return v;
-        }
-        __half hq = __float2half_rn(v * F16_SCALE);
-        pop_st(const_cast<__half *>(hp(d.fdst, d.N)) + e, hq);
-        return __half2float(hq) * F16_INV_SCALE;
-    }
     static __device__ __forceinline__ float st_one(void *g, int q, long long i, long long N, float v) {
         if (q == 0) {
             pop_st(reinterpret_cast<float *>(g) + i, v);
@@ -869,19 +841,19 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
 }
 
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
-template <int S, bool IDX32>
+template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
 
 // one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
 // consecutive z (amortises the launch of blocks that meet only gas)
-template <int S, bool IDX32>
+template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(Dev d) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     int z0 = blockIdx.z * LBMFS_BULK_ZB;
     int z1 = min(z0 + LBMFS_BULK_ZB, d.nz);
 #pragma unroll 1
-    for (int z = z0; z < z1; ++z) liquid_cell<S, IDX32>(d, x, y, z);
+    for (int z = z0; z < z1; ++z) liquid_cell<S>(d, x, y, z);
 }
 
 template <int S>
@@ -901,25 +873,6 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         void *g = d.fdst;
         const long long N = d.N;
         float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st_one(g, q, i, N, v); });
-        if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
-    }
-}
-
-template <int S>
-__device__ __forceinline__ void collide_store32(const Dev &d, typename Sto<S>::R *fp, int i32) {
-    using P = Sto<S>;
-    if constexpr (!P::shifted) {
-        double fn[Q];
-        collide_d(d, fp, fn);
-        double r = 0.0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            P::st32(d, q, i32 + d.put32[q], fn[q]);
-            r += fn[q];
-        }
-        if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
-    } else {
-        float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st32_one(d, q, i32 + d.put32[q], v); });
         if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
     }
 }
@@ -948,7 +901,7 @@ __device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, 
     collide_store<S>(d, fp, i);
 }
 
-template <int S, bool IDX32>
+template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     using P = Sto<S>;
     using R = typename P::R;
@@ -962,23 +915,15 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
     if (c == CL_L && interior) {
         // no obstacle or wall in the neighbourhood and a liquid cell never
         // touches gas: plain pull from the 18 neighbours, no flag loads
-        if constexpr (IDX32) {
-            const int i32 = (int)i;
+        const long long N = d.N;
+        const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) fp[q] = P::ld32(d, q, i32 + d.pull32[q]);
-            collide_store32<S>(d, fp, i32);
-            return;
-        } else {
-            const long long N = d.N;
-            const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
-            fp[0] = P::ld(d.fsrc, 0, i, N);
-        }
+        for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
+        fp[0] = P::ld(d.fsrc, 0, i, N);
     } else {
         gather_general<S>(d, x, y, z, i, fp);
     }
-    collide_store<S>(d, fp, i);  // one copy of the general collision in the kernel
+    collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
 }
 
 // ---------------------------------------- software-pipelined bulk kernel
@@ -1973,11 +1918,9 @@ template <int S> struct Launch {
                 dim3 pgrid(grid.x, grid.y, (d.nz + LBMFS_BULK_PIPE_ZB - 1) / LBMFS_BULK_PIPE_ZB);
                 if (d.bulk == BULK_TMA) k_liquid_tma<S><<<grid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
                 else if (d.bulk == BULK_PIPE) k_liquid_pipe<S><<<pgrid, BULK_THREADS, 0, st>>>(d);
-                else if (d.idx32) k_liquid<S, true><<<grid, BULK_THREADS, 0, st>>>(d);
-                else k_liquid<S, false><<<grid, BULK_THREADS, 0, st>>>(d);
+                else k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
             } else {
-                if (d.idx32) k_liquid<S, true><<<grid, BULK_THREADS, 0, st>>>(d);
-                else k_liquid<S, false><<<grid, BULK_THREADS, 0, st>>>(d);
+                k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
             }
         }
         mark();
