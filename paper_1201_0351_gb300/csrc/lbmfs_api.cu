@@ -201,17 +201,17 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.eps = p->eps;
     d.cap = (uint32_t)N;
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
-    // bulk-kernel variant (float storages): the software-pipelined kernel by
-    // default; LBMFS_BULK=plain|pipe|tma selects another one (the TMA-staged
-    // kernel needs rows of 16-byte multiples and measured slower)
-    d.bulk = BULK_PIPE;
+    // bulk-kernel variant (float storages): direct loads by default;
+    // LBMFS_BULK=pipe|tma selects the shared-memory staged variants (both
+    // measured slower on GB300; the TMA one needs rows of 16-byte multiples)
+    d.bulk = BULK_PLAIN;
     if (const char *v = getenv("LBMFS_BULK")) {
-        if (!strcmp(v, "plain")) d.bulk = BULK_PLAIN;
+        if (!strcmp(v, "pipe")) d.bulk = BULK_PIPE;
         else if (!strcmp(v, "tma")) d.bulk = BULK_TMA;
     }
     if (d.bulk == BULK_TMA &&
         !((p->storage == LBM_FS_F32 && p->nx % 4 == 0) || (p->storage == LBM_FS_F16S && p->nx % 8 == 0)))
-        d.bulk = BULK_PIPE;
+        d.bulk = BULK_PLAIN;
     size_t fb = storage_bytes(p->storage, N);
     size_t nb4 = ((size_t)N + 3) & ~(size_t)3;
     d.flags = (uint8_t *)h->alloc(nb4);
