@@ -209,7 +209,8 @@ def e2e_run(sc, storage, steps):
     h2d = sc.flags.nbytes + sc.fill.nbytes + sc.rho.nbytes
     d2h = sim.nbodies * C_BODY_BYTES
     return dict(value=n * steps / (t1 - t0) / 1e6, unit="MLUPS", h2d_bytes_per_step=h2d // steps,
-                d2h_bytes_per_step=d2h)
+                d2h_bytes_per_step=d2h, steps=steps,
+                covers="create from host arrays, then every step lbm_fs_step + lbm_fs_body_states")
 
 
 def cpu_baseline(sc_full, target_s=15.0):
@@ -261,6 +262,7 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=0, help="steps of the FP64 variant (default steps // 10)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end run (default: the workload's job length)")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     config = {"workload": "wave tank %dx%dx%d, %d free boxes 24x12x8, tau 0.52, g 1e-5" % (
@@ -308,7 +310,7 @@ def main():
         ms = float(t.item())
     n = sc.nx * sc.ny * sc.nz
     value = ws * n * args.steps / (ms * 1e-3) / 1e6
-    e2e = e2e_run(sc, "f32", max(10, min(args.steps, 50)))
+    e2e = e2e_run(sc, "f32", args.e2e_steps or sc.steps)
     e2e["value"] *= ws
     if rank != 0:
         return 0
