@@ -193,6 +193,72 @@ lbm_fs_status lbm_fs_sync(lbm_fs *h);
 lbm_fs_status lbm_fs_kernel_times(lbm_fs *h, int32_t nsteps, double *ms,
                                   const char **names, int32_t cap, int32_t *nk);
 
+/* ---- Batched form: many independent tanks stepped together.
+ *
+ * The paper steps one domain; stepping many small scenarios (a sweep over heel
+ * angles, densities and resolutions) one handle at a time leaves the GPU idle
+ * between a small tank's short kernels.  A batch owns `count` tanks, each an
+ * ordinary simulation created from params[k] (same storage for all; the
+ * batch runs on params[0].stream and uses params[0].use_graphs and its
+ * allocator for its own buffers).  Every kernel of a step is launched once
+ * for all tanks (at most 64 tanks per launch; larger batches use one launch
+ * per group of 64): its blocks walk a packed table of (tank, block) entries,
+ * and the bulk stream + collide kernel runs as a persistent grid over that
+ * table.  The per-cell arithmetic is that of the single-tank path, so each
+ * tank's results equal those of lbm_fs_step on the same tank.
+ *
+ * lbm_fs_batch_create validates every params[k] like lbm_fs_create (the first
+ * failure is returned, with k in the error text) and limits each tank to
+ * 65535 cells per axis.  *out owns every tank until lbm_fs_batch_destroy. */
+typedef struct lbm_fs_batch lbm_fs_batch; /* opaque; owned by the library */
+lbm_fs_status lbm_fs_batch_create(const lbm_fs_params *params, int32_t count, lbm_fs_batch **out);
+lbm_fs_status lbm_fs_batch_destroy(lbm_fs_batch *b);
+
+/* Handle of tank k (owned by the batch).  It serves lbm_fs_add_box (between
+ * batch steps), lbm_fs_forces, lbm_fs_body_state(s), lbm_fs_read_fields,
+ * lbm_fs_stats and lbm_fs_sync; lbm_fs_step, lbm_fs_kernel_times and
+ * lbm_fs_destroy on it return LBM_FS_ESTATE. */
+lbm_fs_status lbm_fs_batch_tank(lbm_fs_batch *b, int32_t k, lbm_fs **out);
+
+/* Enqueues nsteps steps of every tank and returns without waiting. */
+lbm_fs_status lbm_fs_batch_step(lbm_fs_batch *b, int32_t nsteps);
+
+/* Synchronises and reports the first sticky device error of any tank. */
+lbm_fs_status lbm_fs_batch_sync(lbm_fs_batch *b);
+
+/* Launch configuration of a batch:
+ *   zb          z-planes per bulk tile (1..8);
+ *   bulk_blocks persistent grid of the bulk kernel (0: one block per tile);
+ *   list_cells  nx*ny cells of a tank per block of the worklist kernels
+ *               (a tank gets ceil(nx*ny / list_cells) blocks, at most 304);
+ *   bulk_ms     (autotune output) time of one bulk launch with this setting. */
+typedef struct {
+    int32_t zb;
+    int32_t bulk_blocks;
+    int32_t list_cells;
+    int32_t pad;
+    double bulk_ms;
+} lbm_fs_batch_config_t;
+
+/* Times the batched bulk kernel over a set of candidate tilings (zb in
+ * {1, 2, 4, 8}; persistent grids of 1, 2 and 4 times the resident blocks,
+ * and one block per tile) on the current state and keeps the fastest;
+ * *out (may be NULL) receives it.  The state is not advanced: the timed
+ * launches write only the second population grid (rewritten by the next
+ * step), and the worklist counters and mass ledger are restored.  Call it
+ * between steps; the interface-cell count that lbm_fs_stats reports reads 0
+ * until the next step. */
+lbm_fs_status lbm_fs_batch_autotune(lbm_fs_batch *b, lbm_fs_batch_config_t *out);
+lbm_fs_status lbm_fs_batch_set_config(lbm_fs_batch *b, const lbm_fs_batch_config_t *c);
+lbm_fs_status lbm_fs_batch_get_config(lbm_fs_batch *b, lbm_fs_batch_config_t *c);
+
+/* As lbm_fs_kernel_times, for the batched launches (summed over all groups of
+ * 64 tanks); *launches (may be NULL) receives the batch's kernel launches
+ * since creation. */
+lbm_fs_status lbm_fs_batch_kernel_times(lbm_fs_batch *b, int32_t nsteps, double *ms,
+                                        const char **names, int32_t cap, int32_t *nk);
+lbm_fs_status lbm_fs_batch_launches(lbm_fs_batch *b, int64_t *launches, int64_t *steps);
+
 const char *lbm_fs_last_error_string(void);
 int32_t lbm_fs_version(void);
 

@@ -1,7 +1,7 @@
 """Builds libgb300_lbmfs.so (sm_103a) in-tree with nvcc.
 
-Four translation units compile in parallel: the host API and one kernel unit
-per population storage.  The double-precision unit is compiled with
+The translation units compile in parallel: the host API, the batched form,
+one kernel unit per population storage and the allocation-free reduction.  The double-precision unit is compiled with
 -fmad=false (no fused multiply-add) so that it rounds every operation exactly
 as the plain CPU restatement of the method does.
 """
@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 UNITS = {
     "lbmfs_api.cu": [],
+    "lbmfs_batch.cu": [],
     "kernels_f64.cu": ["-fmad=false"],
     "kernels_f32.cu": [],
     "kernels_f16s.cu": [],

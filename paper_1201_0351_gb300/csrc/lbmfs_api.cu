@@ -10,14 +10,18 @@
 #include <vector>
 
 #include "lbm_fs.h"
+#include "lbmfs_handle.h"
 #include "lbmfs_internal.h"
 
 using namespace lbmfs;
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
 
-lbm_fs_status fail(lbm_fs_status s, const char *fmt, const char *detail = nullptr) {
+namespace lbmfs {
+
+lbm_fs_status fail(lbm_fs_status s, const char *fmt, const char *detail) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, detail ? detail : "");
     g_err = buf;
@@ -31,61 +35,13 @@ lbm_fs_status cuda_fail(cudaError_t e, const char *where) {
     return e == cudaErrorMemoryAllocation ? LBM_FS_ENOMEM : LBM_FS_ECUDA;
 }
 
-#define CK(call)                                              \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
-    } while (0)
-}  // namespace
-
-struct lbm_fs {
-    lbm_fs_params p;
-    KernelSet ks;
-    Dev d[2];  // d[0] streams A -> B, d[1] streams B -> A
-    int cur = 0;
-    cudaStream_t st = nullptr;
-    cudaStream_t cap_st = nullptr;
-    std::vector<void *> allocs;
-    int nb = 0;
-    bool started = false;
-    int64_t step = 0;
-    int64_t launches = 0;
-    int per_step = 0;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int graph_nb = -1;
-    bool dead = false;
-
-    void *alloc(size_t bytes) {
-        void *ptr = nullptr;
-        if (bytes == 0) bytes = 4;
-        if (p.dev_alloc) {
-            ptr = p.dev_alloc(bytes, p.alloc_ctx);
-        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            ptr = nullptr;
-        }
-        if (ptr) allocs.push_back(ptr);
-        return ptr;
-    }
-    void release() {
-        for (int k = 0; k < 2; ++k)
-            if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
-        for (void *ptr : allocs) {
-            if (p.dev_free) p.dev_free(ptr, p.alloc_ctx);
-            else cudaFree(ptr);
-        }
-        allocs.clear();
-        if (cap_st) cudaStreamDestroy(cap_st);
-    }
-};
-
-namespace {
-
 lbm_fs_status check_handle(lbm_fs *h) {
     if (!h) return fail(LBM_FS_EINVAL, "null handle%s");
     if (h->dead) return fail(LBM_FS_ESTATE, "handle is in a failed state%s");
     return LBM_FS_OK;
 }
+
+#define CK LBMFS_CK
 
 lbm_fs_status read_status(lbm_fs *h) {
     uint32_t st = 0;
@@ -97,6 +53,18 @@ lbm_fs_status read_status(lbm_fs *h) {
     if (st & ST_LIQUID_GAS) return fail(LBM_FS_EUNSTABLE, "a liquid cell touched a gas cell (open interface layer)%s");
     return LBM_FS_OK;
 }
+
+void begin_mass(lbm_fs *h) {
+    if (h->started) return;
+    h->ks.liquid_mass(h->d[h->cur], h->st);
+    cudaMemcpyAsync(h->d[0].ledger + LG_MASS0, h->d[0].ledger + LG_MASS, sizeof(double), cudaMemcpyDeviceToDevice,
+                    h->st);
+    h->started = true;
+}
+
+}  // namespace lbmfs
+
+namespace {
 
 lbm_fs_status capture_graphs(lbm_fs *h) {
     for (int k = 0; k < 2; ++k) {
@@ -291,6 +259,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
 
 lbm_fs_status lbm_fs_destroy(lbm_fs *h) {
     if (!h) return fail(LBM_FS_EINVAL, "null handle%s");
+    if (h->owner) return fail(LBM_FS_ESTATE, "the tank belongs to a batch (lbm_fs_batch_destroy frees it)%s");
     cudaStreamSynchronize(h->st);
     h->release();
     delete h;
@@ -338,15 +307,12 @@ lbm_fs_status lbm_fs_add_box(lbm_fs *h, const lbm_fs_box *b, int32_t *out_id) {
 lbm_fs_status lbm_fs_step(lbm_fs *h, int32_t nsteps) {
     lbm_fs_status s = check_handle(h);
     if (s) return s;
+    if (h->owner) return fail(LBM_FS_ESTATE, "the tank belongs to a batch (step it with lbm_fs_batch_step)%s");
     if (nsteps < 0) return fail(LBM_FS_EINVAL, "nsteps must be >= 0%s");
     if (nsteps == 0) return LBM_FS_OK;
     cudaStream_t st = h->st;
-    if (!h->started) {
-        h->ks.liquid_mass(h->d[h->cur], st);
-        CK(cudaMemcpyAsync(h->d[0].ledger + LG_MASS0, h->d[0].ledger + LG_MASS, sizeof(double),
-                           cudaMemcpyDeviceToDevice, st));
-        h->started = true;
-    }
+    begin_mass(h);
+    CK(cudaGetLastError());
     if (h->p.use_graphs && h->graph_nb != h->nb) {
         s = capture_graphs(h);
         if (s) return s;
@@ -498,18 +464,15 @@ lbm_fs_status lbm_fs_stats(lbm_fs *h, lbm_fs_stats_t *out) {
 lbm_fs_status lbm_fs_kernel_times(lbm_fs *h, int32_t nsteps, double *ms, const char **names, int32_t cap, int32_t *nk) {
     lbm_fs_status s = check_handle(h);
     if (s) return s;
+    if (h->owner) return fail(LBM_FS_ESTATE, "the tank belongs to a batch (use lbm_fs_batch_kernel_times)%s");
     if (nsteps <= 0 || !ms || cap <= 0) return fail(LBM_FS_EINVAL, "bad arguments%s");
     const int K = h->ks.nkernels;
     std::vector<cudaEvent_t> ev(K + 1);
     for (auto &x : ev) CK(cudaEventCreate(&x));
     std::vector<double> acc(K, 0.0);
     cudaStream_t st = h->st;
-    if (!h->started) {
-        h->ks.liquid_mass(h->d[h->cur], st);
-        CK(cudaMemcpyAsync(h->d[0].ledger + LG_MASS0, h->d[0].ledger + LG_MASS, sizeof(double),
-                           cudaMemcpyDeviceToDevice, st));
-        h->started = true;
-    }
+    begin_mass(h);
+    CK(cudaGetLastError());
     for (int32_t it = 0; it < nsteps; ++it) {
         int n = h->ks.step(h->d[h->cur], st, nullptr, ev.data());
         CK(cudaGetLastError());

@@ -73,6 +73,44 @@ struct Dev {
 // TMA-staged rows (needs 16-byte aligned rows)
 enum { BULK_PLAIN = 0, BULK_PIPE = 1, BULK_TMA = 2 };
 
+// ---- batched form: many tanks stepped by one launch per kernel
+//
+// The descriptors of up to BATCH_TANKS tanks travel by value in the kernel
+// parameter space (read-only, served by the constant cache); each launch
+// walks a packed block table whose entries name a tank and the block of that
+// tank's own grid the entry stands for.
+constexpr int BATCH_TANKS = 64;
+struct TankSet {
+    Dev d[BATCH_TANKS];
+};
+static_assert(sizeof(TankSet) + 64 <= 32764, "tank descriptors must fit the kernel parameter space");
+
+struct Tile {
+    uint16_t tank, x, y, z, nx, ny, nz, pad;  // tank; block (x, y, z) of a (nx, ny, nz) grid
+};
+
+// block tables by launch shape
+enum {
+    SH_FORCE = 0,  // (FORCE_BLOCKS, bodies): forces, remap cover / pending
+    SH_BULK,       // (ceil(nx / BULK_THREADS), ny, ceil(nz / zb)): bulk stream + collide
+    SH_IFACE,      // (2 lb): interface cells
+    SH_LIST,       // (lb): conversion worklists, neighbour-bit refresh
+    SH_BODY,       // (bodies): rigid-body step
+    SH_ONE,        // (1) per tank with bodies: remap resolution
+    SH_TANK,       // (1) per tank: counter reset
+    SH_COUNT
+};
+struct Shape {
+    const Tile *table;  // device
+    unsigned n;         // entries
+    unsigned grid;      // blocks of the launch (each walks entries grid apart)
+};
+struct BatchLaunch {
+    const TankSet *ts;  // host copy, passed by value to every launch
+    Shape sh[SH_COUNT];
+    int zb;             // z-planes per bulk tile
+};
+
 struct KernelSet {
     void (*init_cells)(const Dev &, const uint8_t *flags, const double *fill, const double *rho, const double *vel,
                        cudaStream_t);
@@ -82,6 +120,12 @@ struct KernelSet {
     int (*step)(const Dev &, cudaStream_t, float *ev_ms, cudaEvent_t *ev);
     void (*liquid_mass)(const Dev &, cudaStream_t);  // -> ledger[LG_MASS]
     void (*read_fields)(const Dev &, unsigned mask, void *const *dst, cudaStream_t);
+    // one time step of every tank of a batch chunk; same event protocol and
+    // kernel slots as step
+    int (*batch_step)(const BatchLaunch &, cudaStream_t, cudaEvent_t *ev);
+    // the bulk kernel alone over a chunk (autotuning), and its occupancy
+    void (*batch_bulk)(const BatchLaunch &, cudaStream_t);
+    int (*bulk_blocks_per_sm)();
     int nkernels;
     const char *const *names;
 };

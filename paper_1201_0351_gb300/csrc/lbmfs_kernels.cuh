@@ -594,10 +594,17 @@ __global__ void k_map_body(Dev d, int bi, int book_mass) {
     }
 }
 
+// Coordinates a kernel body runs at: its launch's own block, or one entry of
+// a packed block table when a single launch serves many tanks
+struct VB {
+    unsigned x, y, z, nx, ny, nz;
+};
+__device__ __forceinline__ VB vb_own() { return VB{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z}; }
+
 #define LIST_LOOP(L, var)                                                                                     \
     uint32_t n_##var = wl_count(d, L);                                                                         \
-    for (uint32_t it_##var = blockIdx.x * blockDim.x + threadIdx.x; it_##var < n_##var;                        \
-         it_##var += gridDim.x * blockDim.x)
+    for (uint32_t it_##var = vb.x * blockDim.x + threadIdx.x; it_##var < n_##var;                              \
+         it_##var += vb.nx * blockDim.x)
 
 // neighbour-obstacle bit: set when any of the 18 neighbours is an obstacle or
 // lies beyond a wall face (the bulk kernel then takes its general path)
@@ -665,7 +672,7 @@ __device__ __forceinline__ void nb_refresh_around(const Dev &d, long long i) {
     }
 }
 
-__global__ void k_nb_update(Dev d) {
+__device__ __forceinline__ void nb_update_body(const Dev &d, const VB &vb) {
     {
         LIST_LOOP(WL_COVER, a) nb_refresh_around(d, d.list[WL_COVER][it_a]);
     }
@@ -673,11 +680,12 @@ __global__ void k_nb_update(Dev d) {
         LIST_LOOP(WL_PEND, b) nb_refresh_around(d, d.list[WL_PEND][it_b]);
     }
 }
+__global__ void k_nb_update(const __grid_constant__ Dev d) { nb_update_body(d, vb_own()); }
 
-// ---- C4: momentum exchange at the links into body blockIdx.y (state at t)
+// ---- C4: momentum exchange at the links into body vb.y (state at t)
 template <int S>
-__global__ void __launch_bounds__(256) k_forces(Dev d) {
-    int bi = blockIdx.y;
+__device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
+    int bi = vb.y;
     const Body &b = d.bodies[bi];
     int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, b.lo[2] - 1};
     int hi[3] = {b.hi[0] + 1, b.hi[1] + 1, b.hi[2] + 1};
@@ -693,7 +701,7 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     // z-planes over blocks, (x, y) over the block's 32 x 8 threads; only cells
     // next to an obstacle (neighbour-obstacle bit) can hold links
-    for (int zz = lo[2] + (int)blockIdx.x; zz < hi[2]; zz += gridDim.x) {
+    for (int zz = lo[2] + (int)vb.x; zz < hi[2]; zz += vb.nx) {
         int z = zz < 0 ? zz + d.nz : (zz >= d.nz ? zz - d.nz : zz);
         for (int yy = lo[1] + (int)threadIdx.y; yy < hi[1]; yy += blockDim.y) {
             int y = yy < 0 ? yy + d.ny : (yy >= d.ny ? yy - d.ny : yy);
@@ -817,9 +825,11 @@ __global__ void __launch_bounds__(256) k_forces(Dev d) {
     if (tid < 7) {
         double v = 0.0;
         for (int w = 0; w < 8; ++w) v += sh[w][tid];
-        d.part[((long long)bi * FORCE_BLOCKS + blockIdx.x) * 7 + tid] = v;
+        d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = v;
     }
 }
+template <int S>
+__global__ void __launch_bounds__(256) k_forces(const __grid_constant__ Dev d) { forces_body<S>(d, vb_own()); }
 
 // Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
 // an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
@@ -843,17 +853,22 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
 template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
+template <int S, int ZBMAX>
+__device__ __forceinline__ void liquid_column(const Dev &d, int x, int y, int z0, int z1);
 
 // one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
 // consecutive z (amortises the launch of blocks that meet only gas)
+template <int S, int ZBMAX>
+__device__ __forceinline__ void liquid_body(const Dev &d, const VB &vb, int zb) {
+    int x = vb.x * BULK_THREADS + threadIdx.x;
+    int y = vb.y;
+    int z0 = vb.z * zb;
+    int z1 = min(z0 + zb, d.nz);
+    liquid_column<S, ZBMAX>(d, x, y, z0, z1);
+}
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(Dev d) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    int z0 = blockIdx.z * LBMFS_BULK_ZB;
-    int z1 = min(z0 + LBMFS_BULK_ZB, d.nz);
-#pragma unroll 1
-    for (int z = z0; z < z1; ++z) liquid_cell<S>(d, x, y, z);
+__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(const __grid_constant__ Dev d) {
+    liquid_body<S, LBMFS_BULK_ZB>(d, vb_own(), LBMFS_BULK_ZB);
 }
 
 template <int S>
@@ -924,6 +939,43 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
         gather_general<S>(d, x, y, z, i, fp);
     }
     collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
+}
+
+// The cells (x, y, z0 .. z1-1) of one thread.  The flags of the whole column
+// come in one round of loads, so a thread whose column holds no fluid leaves
+// after one memory latency, and a fluid cell waits on its populations only.
+template <int S, int ZBMAX>
+__device__ __forceinline__ void liquid_column(const Dev &d, int x, int y, int z0, int z1) {
+    using P = Sto<S>;
+    using R = typename P::R;
+    static_assert(ZBMAX <= 8, "flags of a column (z1 - z0 <= ZBMAX) are packed into 64 bits");
+    const bool in = x < d.nx;
+    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
+    long long i = (long long)(in ? x : 0) + sy * (y + (long long)d.ny * z0);
+    const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1;
+    uint64_t fl = 0;
+#pragma unroll
+    for (int k = 0; k < ZBMAX; ++k)
+        if (in && z0 + k < z1) fl |= (uint64_t)d.flags[i + k * sz] << (8 * k);
+    if (fl == 0) return;
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z, i += sz) {
+        const int c = (int)(fl & 0xff);
+        fl >>= 8;
+        wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
+        if ((c & CL_MASK) != CL_L) continue;
+        R fp[Q];
+        if (c == CL_L && inner && z > 0 && z < d.nz - 1) {
+            // no obstacle or wall in the neighbourhood and a liquid cell never
+            // touches gas: plain pull from the 18 neighbours
+#pragma unroll
+            for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            fp[0] = P::ld(d.fsrc, 0, i, N);
+        } else {
+            gather_general<S>(d, x, y, z, i, fp);
+        }
+        collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
+    }
 }
 
 // ---------------------------------------- software-pipelined bulk kernel
@@ -1186,11 +1238,11 @@ __device__ __forceinline__ double fill_seen(const Dev &d, long long ni, double o
 
 // ---- C1 + C2 for interface cells (Sec. 2.2): reconstruction, mass exchange
 template <int S>
-__global__ void __launch_bounds__(128) k_interface(Dev d) {
+__device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
     using P = Sto<S>;
     const long long N = d.N;
     uint32_t n = wl_count(d, WL_IFACE);
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    for (uint32_t it = vb.x * blockDim.x + threadIdx.x; it < n; it += vb.nx * blockDim.x) {
         long long i = d.list[WL_IFACE][it];
         int x, y, z;
         coords(d, i, x, y, z);
@@ -1364,11 +1416,13 @@ __global__ void __launch_bounds__(128) k_interface(Dev d) {
         }
     }
 }
+template <int S>
+__global__ void __launch_bounds__(128) k_interface(const __grid_constant__ Dev d) { interface_body<S>(d, vb_own()); }
 
 // ------------------------------------------------- C3: conversions (Sec. 2.2)
 
 // filled cells: emptied neighbours are kept; gas neighbours become interface
-__global__ void k_conv_filled(Dev d) {
+__device__ __forceinline__ void conv_filled_body(const Dev &d, const VB &vb) {
     LIST_LOOP(WL_FILLED, a) {
         long long i = d.list[WL_FILLED][it_a];
         int x, y, z;
@@ -1389,9 +1443,10 @@ __global__ void k_conv_filled(Dev d) {
         }
     }
 }
+__global__ void k_conv_filled(const __grid_constant__ Dev d) { conv_filled_body(d, vb_own()); }
 
 // still-emptied cells: liquid neighbours become interface
-__global__ void k_conv_emptied(Dev d) {
+__device__ __forceinline__ void conv_emptied_body(const Dev &d, const VB &vb) {
     LIST_LOOP(WL_EMPTIED, a) {
         long long i = d.list[WL_EMPTIED][it_a];
         if (!(d.cmark[i] & MK_EMPTIED)) continue;
@@ -1410,11 +1465,12 @@ __global__ void k_conv_emptied(Dev d) {
         }
     }
 }
+__global__ void k_conv_emptied(const __grid_constant__ Dev d) { conv_emptied_body(d, vb_own()); }
 
 // new interface cells: from gas f = f_eq(mean rho, mean u) of the liquid and
 // interface neighbours, m = 0; from liquid m = rho
 template <int S>
-__global__ void k_conv_init(Dev d) {
+__device__ __forceinline__ void conv_init_body(const Dev &d, const VB &vb) {
     {
         LIST_LOOP(WL_NEWG, a) {
             long long i = d.list[WL_NEWG][it_a];
@@ -1451,8 +1507,10 @@ __global__ void k_conv_init(Dev d) {
         }
     }
 }
+template <int S>
+__global__ void k_conv_init(const __grid_constant__ Dev d) { conv_init_body<S>(d, vb_own()); }
 
-__global__ void k_conv_flags(Dev d) {
+__device__ __forceinline__ void conv_flags_body(const Dev &d, const VB &vb) {
     {
         LIST_LOOP(WL_FILLED, a) set_cls(d, d.list[WL_FILLED][it_a], CL_L);
     }
@@ -1469,6 +1527,7 @@ __global__ void k_conv_flags(Dev d) {
         LIST_LOOP(WL_NEWL, e) set_cls(d, d.list[WL_NEWL][it_e], CL_I);
     }
 }
+__global__ void k_conv_flags(const __grid_constant__ Dev d) { conv_flags_body(d, vb_own()); }
 
 // interface neighbours of converted cells receive excess mass
 __device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
@@ -1487,7 +1546,7 @@ __device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
     }
 }
 
-__global__ void k_conv_claim(Dev d) {
+__device__ __forceinline__ void conv_claim_body(const Dev &d, const VB &vb) {
     {
         LIST_LOOP(WL_FILLED, a) claim_receivers(d, d.list[WL_FILLED][it_a]);
     }
@@ -1498,6 +1557,7 @@ __global__ void k_conv_claim(Dev d) {
         }
     }
 }
+__global__ void k_conv_claim(const __grid_constant__ Dev d) { conv_claim_body(d, vb_own()); }
 
 // k(x): interface neighbours of a converted cell (classes after conversion)
 __device__ __forceinline__ int iface_neighbours(const Dev &d, long long i) {
@@ -1519,7 +1579,7 @@ __device__ __forceinline__ double excess(const Dev &d, long long i, uint8_t mk) 
 
 // receivers gather e(x) / k(x) over their converted neighbours in q order
 template <int S>
-__global__ void k_conv_excess(Dev d) {
+__device__ __forceinline__ void conv_excess_body(const Dev &d, const VB &vb) {
     LIST_LOOP(WL_RECV, a) {
         long long i = d.list[WL_RECV][it_a];
         int x, y, z;
@@ -1538,10 +1598,12 @@ __global__ void k_conv_excess(Dev d) {
         d.phidst[i] = m / cell_density<S>(d, d.fdst, i);
     }
 }
+template <int S>
+__global__ void k_conv_excess(const __grid_constant__ Dev d) { conv_excess_body<S>(d, vb_own()); }
 
 // mass that found no interface neighbour goes to the ledger; marks are cleared
 template <int S>
-__global__ void k_conv_finish(Dev d) {
+__device__ __forceinline__ void conv_finish_body(const Dev &d, const VB &vb) {
     {
         LIST_LOOP(WL_FILLED, a) {
             long long i = d.list[WL_FILLED][it_a];
@@ -1567,12 +1629,14 @@ __global__ void k_conv_finish(Dev d) {
         LIST_LOOP(WL_RECV, g) d.cmark[d.list[WL_RECV][it_g]] = 0;
     }
 }
+template <int S>
+__global__ void k_conv_finish(const __grid_constant__ Dev d) { conv_finish_body<S>(d, vb_own()); }
 
 // ----------------------------------------------- C5: rigid-body update
 
 // one warp per body: fixed-order sum of the force partials, then the update
-__global__ void k_bodies(Dev d) {
-    int bi = blockIdx.x;
+__device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
+    int bi = vb.x;
     Body &b = d.bodies[bi];
     int lane = threadIdx.x;
     double acc[7];
@@ -1659,16 +1723,17 @@ __global__ void k_bodies(Dev d) {
     for (int k = 0; k < 4; ++k) b.q[k] = nq[k] / norm;
     body_bounds(d, b);
 }
+__global__ void k_bodies(const __grid_constant__ Dev d) { bodies_body(d, vb_own()); }
 
 // ----------------------------------------------- C6: remap (Sec. 2.3, 2.4)
 
-// cells inside body blockIdx.y at its new pose become obstacle
+// cells inside body vb.y at its new pose become obstacle
 template <int S>
-__global__ void k_remap_cover(Dev d) {
-    int bi = blockIdx.y;
+__device__ __forceinline__ void remap_cover_body(const Dev &d, const VB &vb) {
+    int bi = vb.y;
     const Body &b = d.bodies[bi];
     long long n = range_count(b.lo, b.hi);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = vb.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)vb.nx * blockDim.x) {
         int x, y, z;
         range_cell(d, b.lo, b.hi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
@@ -1682,13 +1747,15 @@ __global__ void k_remap_cover(Dev d) {
         d.bid[i] = (uint8_t)bi;
     }
 }
+template <int S>
+__global__ void k_remap_cover(const __grid_constant__ Dev d) { remap_cover_body<S>(d, vb_own()); }
 
-// obstacle cells of body blockIdx.y outside its new pose are pending
-__global__ void k_remap_pending(Dev d) {
-    int bi = blockIdx.y;
+// obstacle cells of body vb.y outside its new pose are pending
+__device__ __forceinline__ void remap_pending_body(const Dev &d, const VB &vb) {
+    int bi = vb.y;
     const Body &b = d.bodies[bi];
     long long n = range_count(b.plo, b.phi);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = vb.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)vb.nx * blockDim.x) {
         int x, y, z;
         range_cell(d, b.plo, b.phi, k, x, y, z);
         long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
@@ -1697,11 +1764,12 @@ __global__ void k_remap_pending(Dev d) {
         wl_append(d, pend, WL_PEND, (uint32_t)i);
     }
 }
+__global__ void k_remap_pending(const __grid_constant__ Dev d) { remap_pending_body(d, vb_own()); }
 
 // Jacobi passes of the obstacle-to-fluid rule over the pending cells, closure,
 // uncovered-mass ledger (one block)
 template <int S>
-__global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
+__device__ __forceinline__ void remap_resolve_body(const Dev &d, const VB &vb) {
     uint32_t n = wl_count(d, WL_PEND);
     if (n == 0) return;
     __shared__ int s_any;
@@ -1814,6 +1882,8 @@ __global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(Dev d) {
         d.ledger[LG_UNCOVERED] += t;
     }
 }
+template <int S>
+__global__ void __launch_bounds__(REMAP_THREADS) k_remap_resolve(const __grid_constant__ Dev d) { remap_resolve_body<S>(d, vb_own()); }
 
 // ------------------------------------------------------ reductions, output
 
@@ -1875,6 +1945,57 @@ __global__ void k_read_fields(Dev d, unsigned mask, uint8_t *flags, double *fill
 }
 
 // ------------------------------------------------------------ launchers
+
+// ------------------------------------------------------ batched launches
+//
+// One launch serves all tanks of a TankSet: block b runs the table entries
+// b, b + gridDim.x, ... (a persistent walk when the grid is smaller than the
+// table), each as the block of its tank's own grid that the entry names, with
+// the block size of the single-tank launch.  The per-cell work is the
+// single-tank kernels' own code.
+template <class K>
+__global__ void __launch_bounds__(K::THREADS, K::MINB)
+    k_batch(const __grid_constant__ TankSet ts, const Tile *__restrict__ table, unsigned n, int zb) {
+    for (unsigned t = blockIdx.x; t < n; t += gridDim.x) {
+        const Tile e = table[t];
+        const VB vb{e.x, e.y, e.z, e.nx, e.ny, e.nz};
+        K::run(ts.d[e.tank], vb, zb);
+        __syncthreads();  // the next entry's body reuses this one's shared memory
+    }
+}
+
+#define LBMFS_BATCH_BODY(NAME, THR, MB, CALL)                                                 \
+    struct NAME {                                                                              \
+        static constexpr int THREADS = THR, MINB = MB;                                         \
+        static __device__ __forceinline__ void run(const Dev &d, const VB &vb, int zb) { CALL; } \
+    };
+struct BkReset {
+    static constexpr int THREADS = 32, MINB = 1;
+    static __device__ __forceinline__ void run(const Dev &d, const VB &, int) {
+        if (threadIdx.x < WL_COUNT) d.cnt[threadIdx.x] = 0;
+    }
+};
+template <int S> LBMFS_BATCH_BODY(BkForces, 256, 1, forces_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, 8>(d, vb, zb)))
+template <int S> LBMFS_BATCH_BODY(BkInterface, 128, 1, interface_body<S>(d, vb))
+LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
+LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkConvInit, LIST_THREADS, 1, conv_init_body<S>(d, vb))
+LBMFS_BATCH_BODY(BkConvFlags, LIST_THREADS, 1, conv_flags_body(d, vb))
+LBMFS_BATCH_BODY(BkConvClaim, LIST_THREADS, 1, conv_claim_body(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkConvExcess, LIST_THREADS, 1, conv_excess_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkConvFinish, LIST_THREADS, 1, conv_finish_body<S>(d, vb))
+LBMFS_BATCH_BODY(BkBodies, 32, 1, bodies_body(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkRemapCover, 256, 1, remap_cover_body<S>(d, vb))
+LBMFS_BATCH_BODY(BkRemapPending, 256, 1, remap_pending_body(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkRemapResolve, REMAP_THREADS, 1, remap_resolve_body<S>(d, vb))
+LBMFS_BATCH_BODY(BkNbUpdate, LIST_THREADS, 1, nb_update_body(d, vb))
+#undef LBMFS_BATCH_BODY
+
+template <class K> void batch_launch(const BatchLaunch &b, int sh, dim3 block, cudaStream_t st) {
+    const Shape &x = b.sh[sh];
+    if (x.n) k_batch<K><<<x.grid, block, 0, st>>>(*b.ts, x.table, x.n, b.zb);
+}
 
 template <int S> struct Launch {
     static void init_cells(const Dev &d, const uint8_t *flags, const double *fill, const double *rho, const double *vel,
@@ -1954,6 +2075,62 @@ template <int S> struct Launch {
     }
 };
 
+// The batched counterpart of Launch<S>::step (same kernel slots).
+template <int S> struct BatchStep {
+    static int step(const BatchLaunch &b, cudaStream_t st, cudaEvent_t *ev) {
+        int k = 0;
+        auto mark = [&]() {
+            if (ev) cudaEventRecord(ev[k], st);
+            ++k;
+        };
+        mark();
+        batch_launch<BkReset>(b, SH_TANK, 32, st);
+        mark();
+        batch_launch<BkForces<S>>(b, SH_FORCE, dim3(32, 8), st);
+        mark();
+        batch_launch<BkLiquid<S>>(b, SH_BULK, BULK_THREADS, st);
+        mark();
+        batch_launch<BkInterface<S>>(b, SH_IFACE, 128, st);
+        mark();
+        batch_launch<BkConvFilled>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvEmptied>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvInit<S>>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvFlags>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvClaim>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvExcess<S>>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkConvFinish<S>>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        batch_launch<BkBodies>(b, SH_BODY, 32, st);
+        mark();
+        batch_launch<BkRemapCover<S>>(b, SH_FORCE, 256, st);
+        mark();
+        batch_launch<BkRemapPending>(b, SH_FORCE, 256, st);
+        mark();
+        batch_launch<BkRemapResolve<S>>(b, SH_ONE, REMAP_THREADS, st);
+        mark();
+        batch_launch<BkNbUpdate>(b, SH_LIST, LIST_THREADS, st);
+        mark();
+        int n = 0;
+        const int shapes[] = {SH_TANK, SH_FORCE, SH_BULK, SH_IFACE, SH_LIST, SH_LIST, SH_LIST, SH_LIST, SH_LIST,
+                              SH_LIST, SH_LIST, SH_BODY, SH_FORCE, SH_FORCE, SH_ONE, SH_LIST};
+        for (int sh : shapes) n += b.sh[sh].n ? 1 : 0;
+        return n;
+    }
+    static void bulk(const BatchLaunch &b, cudaStream_t st) { batch_launch<BkLiquid<S>>(b, SH_BULK, BULK_THREADS, st); }
+    static int bulk_blocks_per_sm() {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BkLiquid<S>>, BULK_THREADS, 0) != cudaSuccess)
+            return 1;
+        return nb > 0 ? nb : 1;
+    }
+};
+
 inline const char *const *kernel_names() {
     static const char *const n[] = {"reset_counters", "forces", "liquid", "interface", "conv_filled",
                                     "conv_emptied",    "conv_init", "conv_flags", "conv_claim", "conv_excess",
@@ -1969,6 +2146,9 @@ template <int S> KernelSet make_kernel_set() {
     k.step = &Launch<S>::step;
     k.liquid_mass = &Launch<S>::liquid_mass;
     k.read_fields = &Launch<S>::read_fields;
+    k.batch_step = &BatchStep<S>::step;
+    k.batch_bulk = &BatchStep<S>::bulk;
+    k.bulk_blocks_per_sm = &BatchStep<S>::bulk_blocks_per_sm;
     k.nkernels = 16;
     k.names = kernel_names();
     return k;

@@ -56,10 +56,18 @@ class lbm_fs_stats_t(C.Structure):
                 ("kernel_launches", C.c_int64), ("wall_source", C.c_double)]
 
 
+class lbm_fs_batch_config_t(C.Structure):
+    _fields_ = [("zb", C.c_int32), ("bulk_blocks", C.c_int32), ("list_cells", C.c_int32), ("pad", C.c_int32),
+                ("bulk_ms", C.c_double)]
+
+
 EXPORTS = ("lbm_fs_create", "lbm_fs_destroy", "lbm_fs_add_box", "lbm_fs_step", "lbm_fs_forces", "lbm_fs_body_state",
            "lbm_fs_body_states",
            "lbm_fs_read_fields", "lbm_fs_stats", "lbm_fs_sync", "lbm_fs_kernel_times", "lbm_fs_last_error_string",
-           "lbm_fs_version", "lbm_fs_liquid_mass_noalloc", "lbm_fs_noalloc_last_error_string")
+           "lbm_fs_version", "lbm_fs_liquid_mass_noalloc", "lbm_fs_noalloc_last_error_string",
+           "lbm_fs_batch_create", "lbm_fs_batch_destroy", "lbm_fs_batch_tank", "lbm_fs_batch_step",
+           "lbm_fs_batch_sync", "lbm_fs_batch_autotune", "lbm_fs_batch_set_config", "lbm_fs_batch_get_config",
+           "lbm_fs_batch_kernel_times", "lbm_fs_batch_launches")
 
 _lib = None
 
@@ -101,6 +109,17 @@ def load(build_if_needed: bool = True):
     lib.lbm_fs_liquid_mass_noalloc.argtypes = [P, P, C.c_int64, P, P]
     lib.lbm_fs_noalloc_last_error_string.restype = C.c_char_p
     lib.lbm_fs_noalloc_last_error_string.argtypes = []
+    CFG = C.POINTER(lbm_fs_batch_config_t)
+    lib.lbm_fs_batch_create.argtypes = [C.POINTER(lbm_fs_params), I32, C.POINTER(P)]
+    lib.lbm_fs_batch_destroy.argtypes = [P]
+    lib.lbm_fs_batch_tank.argtypes = [P, I32, C.POINTER(P)]
+    lib.lbm_fs_batch_step.argtypes = [P, I32]
+    lib.lbm_fs_batch_sync.argtypes = [P]
+    lib.lbm_fs_batch_autotune.argtypes = [P, CFG]
+    lib.lbm_fs_batch_set_config.argtypes = [P, CFG]
+    lib.lbm_fs_batch_get_config.argtypes = [P, CFG]
+    lib.lbm_fs_batch_kernel_times.argtypes = [P, I32, D, C.POINTER(C.c_char_p), I32, C.POINTER(I32)]
+    lib.lbm_fs_batch_launches.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     for name in EXPORTS:
         if name not in ("lbm_fs_last_error_string", "lbm_fs_version", "lbm_fs_noalloc_last_error_string"):
             getattr(lib, name).restype = C.c_int
@@ -190,6 +209,67 @@ def lbm_fs_liquid_mass_noalloc(flags_dev: int, mass_dev: int, n: int, out_dev: i
         raise LbmFsError(code, "lbm_fs_liquid_mass_noalloc", load().lbm_fs_noalloc_last_error_string().decode())
 
 
+def lbm_fs_batch_create(params: Sequence[lbm_fs_params]):
+    arr = (lbm_fs_params * len(params))(*params)
+    b = C.c_void_p()
+    _check(load().lbm_fs_batch_create(arr, len(params), C.byref(b)), "lbm_fs_batch_create")
+    return b
+
+
+def lbm_fs_batch_destroy(b):
+    _check(load().lbm_fs_batch_destroy(b), "lbm_fs_batch_destroy")
+
+
+def lbm_fs_batch_tank(b, k: int):
+    h = C.c_void_p()
+    _check(load().lbm_fs_batch_tank(b, int(k), C.byref(h)), "lbm_fs_batch_tank")
+    return h
+
+
+def lbm_fs_batch_step(b, nsteps: int):
+    _check(load().lbm_fs_batch_step(b, int(nsteps)), "lbm_fs_batch_step")
+
+
+def lbm_fs_batch_sync(b):
+    _check(load().lbm_fs_batch_sync(b), "lbm_fs_batch_sync")
+
+
+def _cfg_dict(c: lbm_fs_batch_config_t) -> dict:
+    return dict(zb=c.zb, bulk_blocks=c.bulk_blocks, list_cells=c.list_cells, bulk_ms=c.bulk_ms)
+
+
+def lbm_fs_batch_autotune(b) -> dict:
+    c = lbm_fs_batch_config_t()
+    _check(load().lbm_fs_batch_autotune(b, C.byref(c)), "lbm_fs_batch_autotune")
+    return _cfg_dict(c)
+
+
+def lbm_fs_batch_get_config(b) -> dict:
+    c = lbm_fs_batch_config_t()
+    _check(load().lbm_fs_batch_get_config(b, C.byref(c)), "lbm_fs_batch_get_config")
+    return _cfg_dict(c)
+
+
+def lbm_fs_batch_set_config(b, zb: int, bulk_blocks: int, list_cells: int):
+    c = lbm_fs_batch_config_t(zb=int(zb), bulk_blocks=int(bulk_blocks), list_cells=int(list_cells))
+    _check(load().lbm_fs_batch_set_config(b, C.byref(c)), "lbm_fs_batch_set_config")
+
+
+def lbm_fs_batch_kernel_times(b, nsteps: int):
+    cap = 32
+    ms = (C.c_double * cap)()
+    names = (C.c_char_p * cap)()
+    nk = C.c_int32(0)
+    _check(load().lbm_fs_batch_kernel_times(b, int(nsteps), ms, names, cap, C.byref(nk)), "lbm_fs_batch_kernel_times")
+    return {names[k].decode(): ms[k] for k in range(nk.value)}
+
+
+def lbm_fs_batch_launches(b):
+    n, st = C.c_int64(0), C.c_int64(0)
+    _check(load().lbm_fs_batch_launches(b, C.byref(n), C.byref(st)), "lbm_fs_batch_launches")
+    return n.value, st.value
+
+
 # ------------------------------------------------------------ convenience
 
 class TorchAllocator:
@@ -230,69 +310,52 @@ def make_box(b) -> lbm_fs_box:
     return box
 
 
-class Simulation:
-    """One handle of the library for a scenario of paper_1201_0351_gb300.inputs.
-
-    storage: 'f64', 'f32' or 'f16s'.  Initial arrays are passed as host buffers
-    (the library uploads them) unless host_init=False, in which case they are
-    first copied to device tensors.
-    """
-
-    def __init__(self, sc, storage: str = "f64", use_graphs: bool = True, torch_alloc: bool = True,
-                 host_init: bool = True, stream=None):
+def scenario_params(sc, storage: str, stream: int, use_graphs: bool, alloc=None, keep=None, device=None):
+    """lbm_fs_params for a scenario of paper_1201_0351_gb300.inputs with its
+    initial arrays as host buffers (device tensors when device is given);
+    the buffers are appended to keep and must live until the create call
+    returns."""
+    p = lbm_fs_params()
+    p.nx, p.ny, p.nz, p.periodic = sc.nx, sc.ny, sc.nz, sc.periodic
+    p.tau = sc.tau
+    p.gravity[:] = list(sc.gravity)
+    p.body_accel[:] = list(sc.body_accel)
+    p.rho_gas, p.eps = sc.rho_gas, sc.eps
+    p.storage = STORAGE[storage]
+    keep = [] if keep is None else keep
+    flags = np.ascontiguousarray(sc.flags, np.uint8)
+    fill = np.ascontiguousarray(sc.fill, np.float64)
+    rho = np.ascontiguousarray(sc.rho, np.float64)
+    vel = None if sc.vel is None else np.ascontiguousarray(sc.vel, np.float64).reshape(-1)
+    if device is None:
+        arrs = [flags, fill, rho, vel]
+        keep += arrs
+        p.init_flags, p.init_fill, p.init_rho = (a.ctypes.data for a in arrs[:3])
+        p.init_vel = vel.ctypes.data if vel is not None else None
+        p.init_on_device = 0
+    else:
         import torch
 
-        if not torch.cuda.is_available():
-            raise RuntimeError("the free-surface LBM library needs a CUDA GPU")
-        load()
-        self.torch = torch
-        self.sc = sc
-        self.n = sc.nx * sc.ny * sc.nz
-        self.device = torch.cuda.current_device()
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
-        p = lbm_fs_params()
-        p.nx, p.ny, p.nz, p.periodic = sc.nx, sc.ny, sc.nz, sc.periodic
-        p.tau = sc.tau
-        p.gravity[:] = list(sc.gravity)
-        p.body_accel[:] = list(sc.body_accel)
-        p.rho_gas, p.eps = sc.rho_gas, sc.eps
-        p.storage = STORAGE[storage]
-        self._keep = []
-        flags = np.ascontiguousarray(sc.flags, np.uint8)
-        fill = np.ascontiguousarray(sc.fill, np.float64)
-        rho = np.ascontiguousarray(sc.rho, np.float64)
-        vel = None if sc.vel is None else np.ascontiguousarray(sc.vel, np.float64).reshape(-1)
-        if host_init:
-            arrs = [flags, fill, rho, vel]
-            self._keep += arrs
-            p.init_flags, p.init_fill, p.init_rho = (a.ctypes.data for a in arrs[:3])
-            p.init_vel = vel.ctypes.data if vel is not None else None
-            p.init_on_device = 0
-        else:
-            ts = [torch.from_numpy(a).to(self.device) if a is not None else None for a in (flags, fill, rho, vel)]
-            self._keep += ts
-            p.init_flags, p.init_fill, p.init_rho = (t.data_ptr() for t in ts[:3])
-            p.init_vel = ts[3].data_ptr() if ts[3] is not None else None
-            p.init_on_device = 1
-        if torch_alloc:
-            self.alloc = TorchAllocator(self.device, self.stream.cuda_stream)
-            p.dev_alloc, p.dev_free = self.alloc.c_alloc, self.alloc.c_free
-        p.stream = self.stream.cuda_stream
-        p.use_graphs = 1 if use_graphs else 0
-        self.params = p
-        self.h = lbm_fs_create(p)
-        self._keep = []
-        self.nbodies = 0
-        for b in sc.boxes:
-            self.add_box(b)
+        ts = [torch.from_numpy(a).to(device) if a is not None else None for a in (flags, fill, rho, vel)]
+        keep += ts
+        p.init_flags, p.init_fill, p.init_rho = (t.data_ptr() for t in ts[:3])
+        p.init_vel = ts[3].data_ptr() if ts[3] is not None else None
+        p.init_on_device = 1
+    if alloc is not None:
+        p.dev_alloc, p.dev_free = alloc.c_alloc, alloc.c_free
+    p.stream = stream
+    p.use_graphs = 1 if use_graphs else 0
+    return p
+
+
+class _Handle:
+    """Read-side calls shared by a simulation and a tank of a batch (self.h,
+    self.n, self.device, self.torch, self.nbodies)."""
 
     def add_box(self, b) -> int:
         i = lbm_fs_add_box(self.h, make_box(b))
         self.nbodies += 1
         return i
-
-    def step(self, n: int = 1):
-        lbm_fs_step(self.h, n)
 
     def sync(self):
         lbm_fs_sync(self.h)
@@ -302,9 +365,6 @@ class Simulation:
 
     def stats(self) -> dict:
         return lbm_fs_stats(self.h)
-
-    def kernel_times(self, nsteps: int) -> dict:
-        return lbm_fs_kernel_times(self.h, nsteps)
 
     def fields(self, want_f: bool = False, on_device: bool = False) -> dict:
         n = self.n
@@ -326,9 +386,119 @@ class Simulation:
             res["f"] = out[5].reshape(19, n)
         return res
 
+
+class Simulation(_Handle):
+    """One handle of the library for a scenario of paper_1201_0351_gb300.inputs.
+
+    storage: 'f64', 'f32' or 'f16s'.  Initial arrays are passed as host buffers
+    (the library uploads them) unless host_init=False, in which case they are
+    first copied to device tensors.
+    """
+
+    def __init__(self, sc, storage: str = "f64", use_graphs: bool = True, torch_alloc: bool = True,
+                 host_init: bool = True, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the free-surface LBM library needs a CUDA GPU")
+        load()
+        self.torch = torch
+        self.sc = sc
+        self.n = sc.nx * sc.ny * sc.nz
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.alloc = TorchAllocator(self.device, self.stream.cuda_stream) if torch_alloc else None
+        keep = []
+        p = scenario_params(sc, storage, self.stream.cuda_stream, use_graphs, self.alloc, keep,
+                            None if host_init else self.device)
+        self.params = p
+        self.h = lbm_fs_create(p)
+        del keep
+        self.nbodies = 0
+        for b in sc.boxes:
+            self.add_box(b)
+
+    def step(self, n: int = 1):
+        lbm_fs_step(self.h, n)
+
+    def kernel_times(self, nsteps: int) -> dict:
+        return lbm_fs_kernel_times(self.h, nsteps)
+
     def close(self):
         if getattr(self, "h", None):
             lbm_fs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TankView(_Handle):
+    """Tank k of a Batch: the read-side calls of a simulation (and add_box
+    between batch steps); the batch steps it."""
+
+    def __init__(self, batch, k: int, sc):
+        self.torch = batch.torch
+        self.h = lbm_fs_batch_tank(batch.h, k)
+        self.sc = sc
+        self.n = sc.nx * sc.ny * sc.nz
+        self.device = batch.device
+        self.nbodies = 0
+
+
+class Batch:
+    """Many scenarios stepped together by the batched form of the library
+    (one launch per kernel for all tanks, packed block tables, CUDA graphs)."""
+
+    def __init__(self, scenarios, storage: str = "f16s", use_graphs: bool = True, torch_alloc: bool = True,
+                 stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the free-surface LBM library needs a CUDA GPU")
+        load()
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.alloc = TorchAllocator(self.device, self.stream.cuda_stream) if torch_alloc else None
+        keep = []
+        params = [scenario_params(sc, storage, self.stream.cuda_stream, use_graphs, self.alloc, keep)
+                  for sc in scenarios]
+        self.h = lbm_fs_batch_create(params)
+        del keep
+        self.tanks = [TankView(self, k, sc) for k, sc in enumerate(scenarios)]
+        for t, sc in zip(self.tanks, scenarios):
+            for b in sc.boxes:
+                t.add_box(b)
+        self.cells = sum(t.n for t in self.tanks)
+
+    def step(self, n: int = 1):
+        lbm_fs_batch_step(self.h, n)
+
+    def sync(self):
+        lbm_fs_batch_sync(self.h)
+
+    def autotune(self) -> dict:
+        return lbm_fs_batch_autotune(self.h)
+
+    def config(self) -> dict:
+        return lbm_fs_batch_get_config(self.h)
+
+    def set_config(self, zb: int, bulk_blocks: int, list_cells: int):
+        lbm_fs_batch_set_config(self.h, zb, bulk_blocks, list_cells)
+
+    def kernel_times(self, nsteps: int) -> dict:
+        return lbm_fs_batch_kernel_times(self.h, nsteps)
+
+    def launches(self):
+        return lbm_fs_batch_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_fs_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

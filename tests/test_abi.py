@@ -85,3 +85,22 @@ def test_noalloc_entry_rejects_bad_sizes_on_host():
     assert lib.lbm_fs_liquid_mass_noalloc(p, p, -1, p, None) == lbm_fs.LBM_FS_EINVAL
     assert lib.lbm_fs_liquid_mass_noalloc(p, p, 268435457, p, None) == lbm_fs.LBM_FS_EINVAL
     assert lib.lbm_fs_liquid_mass_noalloc(None, p, 10, p, None) == lbm_fs.LBM_FS_EINVAL
+
+
+def test_batch_rejects_bad_arguments_on_host():
+    lib = lbm_fs.load()
+    out = ctypes.c_void_p()
+    p, keep = _params()
+    assert lib.lbm_fs_batch_create(ctypes.byref(p), 0, ctypes.byref(out)) == lbm_fs.LBM_FS_EINVAL
+    q, keep2 = _params(storage=lbm_fs.LBM_FS_F16S)
+    arr = (lbm_fs.lbm_fs_params * 2)(p, q)
+    assert lib.lbm_fs_batch_create(arr, 2, ctypes.byref(out)) == lbm_fs.LBM_FS_EINVAL
+    assert b"storage" in lib.lbm_fs_last_error_string()
+    big, keep3 = _params(nx=70000)
+    assert lib.lbm_fs_batch_create(ctypes.byref(big), 1, ctypes.byref(out)) == lbm_fs.LBM_FS_EINVAL
+    assert not out.value
+    for name in ("lbm_fs_batch_step", "lbm_fs_batch_sync", "lbm_fs_batch_destroy"):
+        fn = getattr(lib, name)
+        assert (fn(None, 1) if name == "lbm_fs_batch_step" else fn(None)) == lbm_fs.LBM_FS_EINVAL
+    cfg = lbm_fs.lbm_fs_batch_config_t(zb=9, bulk_blocks=0, list_cells=1024)
+    assert lib.lbm_fs_batch_set_config(None, ctypes.byref(cfg)) == lbm_fs.LBM_FS_EINVAL
