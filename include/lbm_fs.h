@@ -209,7 +209,8 @@ lbm_fs_status lbm_fs_kernel_times(lbm_fs *h, int32_t nsteps, double *ms,
  *
  * lbm_fs_batch_create validates every params[k] like lbm_fs_create (the first
  * failure is returned, with k in the error text) and limits each tank to
- * 65535 cells per axis.  *out owns every tank until lbm_fs_batch_destroy. */
+ * 65535 cells per axis and nx*ny <= 8388480.  *out owns every tank until
+ * lbm_fs_batch_destroy. */
 typedef struct lbm_fs_batch lbm_fs_batch; /* opaque; owned by the library */
 lbm_fs_status lbm_fs_batch_create(const lbm_fs_params *params, int32_t count, lbm_fs_batch **out);
 lbm_fs_status lbm_fs_batch_destroy(lbm_fs_batch *b);

@@ -76,6 +76,8 @@ typedef struct {
     double axis[3], damp;
     double F[3], T[3], S;
     double dv[3], dw[3]; /* last velocity / angular-velocity increments (virtual mass) */
+    double Fp[3], Tp[3]; /* the previous step's force and torque */
+    int nF;              /* 1 once Fp, Tp hold a step */
 } body_t;
 
 /* virtual-mass coefficient of the rigid-body update (Schwarz, Kempe and
@@ -608,9 +610,15 @@ static void conversions(orc_sim *s) {
  * update of a body that is light compared with the liquid is unstable with the
  * momentum-exchange force (the bounce-back answers a velocity change within
  * one step: the added-mass instability), so the update uses the virtual-mass
- * scheme: (m + C m_f) dv_{n+1} = F_n + m g + C m_f dv_n, with m_f the mass of
+ * scheme: (m + C m_f) dv_{n+1} = Fh_n + m g + C m_f dv_n, with m_f the mass of
  * liquid of the body's volume and dv the per-step velocity increment; the
- * same for the angular velocity in the body frame.  Position: semi-implicit
+ * same for the angular velocity in the body frame.  Fh_n (and the torque
+ * likewise) is the mean of the momentum-exchange force of this step and the
+ * previous one (the force itself on the first step): near tau = 1/2 the BGK
+ * modes that flip sign every step are barely damped, and a force that flips
+ * with them feeds back through the wall velocity into a growing oscillation
+ * of the body and the liquid under it; the two-step mean removes that
+ * component and leaves slower forcing unchanged.  Position: semi-implicit
  * Euler; orientation: first-order quaternion update and renormalisation. */
 static void bodies_step(orc_sim *s) {
     for (int bi = 0; bi < s->nb; ++bi) {
@@ -620,6 +628,14 @@ static void bodies_step(orc_sim *s) {
             for (int k = 0; k < 3; ++k) b->v[k] = b->w[k] = b->dv[k] = b->dw[k] = 0.0;
             continue;
         }
+        double Fh[3], Th[3];
+        for (int k = 0; k < 3; ++k) {
+            Fh[k] = b->nF ? 0.5 * (b->F[k] + b->Fp[k]) : b->F[k];
+            Th[k] = b->nF ? 0.5 * (b->T[k] + b->Tp[k]) : b->T[k];
+            b->Fp[k] = b->F[k];
+            b->Tp[k] = b->T[k];
+        }
+        b->nF = 1;
         double vol = ((8.0 * b->h[0]) * b->h[1]) * b->h[2];
         double mass = b->dens * vol;
         double I[3] = {(mass / 3.0) * (b->h[1] * b->h[1] + b->h[2] * b->h[2]),
@@ -628,7 +644,7 @@ static void bodies_step(orc_sim *s) {
         double If[3] = {I[0] / b->dens, I[1] / b->dens, I[2] / b->dens}; /* inertia of the displaced liquid */
         double den = mass + VIRTUAL_MASS * vol;
         for (int k = 0; k < 3; ++k) {
-            double num = (b->F[k] + mass * s->grav[k]) + VIRTUAL_MASS * (vol * b->dv[k]);
+            double num = (Fh[k] + mass * s->grav[k]) + VIRTUAL_MASS * (vol * b->dv[k]);
             b->dv[k] = num / den;
             b->v[k] = b->v[k] + b->dv[k];
         }
@@ -638,7 +654,7 @@ static void bodies_step(orc_sim *s) {
         rotation(b->q, R);
         if (base == M_ROT_AXIS) {
             const double *ax = b->axis;
-            double ta = (b->T[0] * ax[0] + b->T[1] * ax[1]) + b->T[2] * ax[2];
+            double ta = (Th[0] * ax[0] + Th[1] * ax[1]) + Th[2] * ax[2];
             double ab[3];
             for (int k = 0; k < 3; ++k) ab[k] = (R[0][k] * ax[0] + R[1][k] * ax[1]) + R[2][k] * ax[2];
             double Ia = (ab[0] * ab[0] * I[0] + ab[1] * ab[1] * I[1]) + ab[2] * ab[2] * I[2];
@@ -651,7 +667,7 @@ static void bodies_step(orc_sim *s) {
             double wb[3], tb[3], L[3], gy[3];
             for (int k = 0; k < 3; ++k) {
                 wb[k] = (R[0][k] * b->w[0] + R[1][k] * b->w[1]) + R[2][k] * b->w[2];
-                tb[k] = (R[0][k] * b->T[0] + R[1][k] * b->T[1]) + R[2][k] * b->T[2];
+                tb[k] = (R[0][k] * Th[0] + R[1][k] * Th[1]) + R[2][k] * Th[2];
                 L[k] = I[k] * wb[k];
             }
             gy[0] = wb[1] * L[2] - wb[2] * L[1];

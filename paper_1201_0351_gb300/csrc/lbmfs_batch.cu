@@ -126,10 +126,10 @@ lbm_fs_status build(lbm_fs_batch *b) {
             tb[SH_TANK].push_back(tile(j, 0, 0, 0, 1, 1, 1));
             for (int y = 0; y < nb; ++y)
                 for (int x = 0; x < FORCE_BLOCKS; ++x) tb[SH_FORCE].push_back(tile(j, x, y, 0, FORCE_BLOCKS, nb, 1));
-            const int gx = (d.nx + BULK_THREADS - 1) / BULK_THREADS, gy = d.ny, gz = (d.nz + b->zb - 1) / b->zb;
+            const int gx = (int)(((long long)d.nx * d.ny + BULK_THREADS - 1) / BULK_THREADS);
+            const int gz = (d.nz + b->zb - 1) / b->zb;
             for (int z = 0; z < gz; ++z)
-                for (int y = 0; y < gy; ++y)
-                    for (int x = 0; x < gx; ++x) tb[SH_BULK].push_back(tile(j, x, y, z, gx, gy, gz));
+                for (int x = 0; x < gx; ++x) tb[SH_BULK].push_back(tile(j, x, 0, z, gx, 1, gz));
             const int lb = list_blocks(t, b->list_cells);
             for (int x = 0; x < 2 * lb; ++x) tb[SH_IFACE].push_back(tile(j, x, 0, 0, 2 * lb, 1, 1));
             for (int x = 0; x < lb; ++x) tb[SH_LIST].push_back(tile(j, x, 0, 0, lb, 1, 1));
@@ -244,8 +244,9 @@ lbm_fs_status lbm_fs_batch_create(const lbm_fs_params *params, int32_t count, lb
     for (int32_t k = 0; k < count; ++k) {
         const lbm_fs_params &p = params[k];
         if (p.storage != params[0].storage) return fail(LBM_FS_EINVAL, "all tanks of a batch share one storage%s");
-        if (p.nx <= 0 || p.ny <= 0 || p.nz <= 0 || p.nx > 65535 || p.ny > 65535 || p.nz > 65535)
-            return fail(LBM_FS_EINVAL, "batch tanks need 1..65535 cells per axis%s");
+        if (p.nx <= 0 || p.ny <= 0 || p.nz <= 0 || p.nx > 65535 || p.ny > 65535 || p.nz > 65535 ||
+            (long long)p.nx * p.ny > 65535ll * BULK_THREADS)
+            return fail(LBM_FS_EINVAL, "batch tanks need 1..65535 cells per axis and nx*ny <= 8388480%s");
     }
     lbm_fs_batch *b = new lbm_fs_batch();
     b->st = (cudaStream_t)params[0].stream;

@@ -40,6 +40,8 @@ struct Body {
     double o[3], h[3], q[4], dens, v[3], w[3], axis[3], damp;
     double dv[3], dw[3];
     double F[3], T[3], S;
+    double Fp[3], Tp[3];  // the previous step's force and torque (rigid-body update)
+    int nF, pad2;         // 1 once Fp, Tp hold a step
     double R[9];        // rotation of q (row-major), recomputed with the pose
     int mode, pad;
     int lo[3], hi[3];   // cells that may be inside at the current pose, [lo, hi)
@@ -129,6 +131,13 @@ struct KernelSet {
     int nkernels;
     const char *const *names;
 };
+
+// The rigid-body update (double precision, independent of the storage) is
+// compiled once, in the unit built without fused multiply-add, and launched
+// from there for every storage: its rounding is then the same in every
+// kernel set and in single-tank and batched launches.
+void launch_bodies(const Dev &d, cudaStream_t st);
+void launch_bodies_batch(const BatchLaunch &b, cudaStream_t st);
 
 KernelSet kernels_f64();
 KernelSet kernels_f32();

@@ -854,17 +854,22 @@ __device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long
 template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
 template <int S, int ZBMAX>
-__device__ __forceinline__ void liquid_column(const Dev &d, int x, int y, int z0, int z1);
+__device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int y, int z0, int z1);
 
 // one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
 // consecutive z (amortises the launch of blocks that meet only gas)
+// A block covers BULK_THREADS consecutive cells of an xy-plane (row ends
+// wrap to the next row, so narrow grids keep every lane busy) for zb
+// consecutive z: grid (ceil(nx ny / BULK_THREADS), 1, ceil(nz / zb)).
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_body(const Dev &d, const VB &vb, int zb) {
-    int x = vb.x * BULK_THREADS + threadIdx.x;
-    int y = vb.y;
-    int z0 = vb.z * zb;
-    int z1 = min(z0 + zb, d.nz);
-    liquid_column<S, ZBMAX>(d, x, y, z0, z1);
+    const unsigned p = vb.x * BULK_THREADS + threadIdx.x;
+    const bool in = p < (unsigned)d.nx * (unsigned)d.ny;
+    const int y = in ? (int)(p / (unsigned)d.nx) : 0;
+    const int x = in ? (int)p - y * d.nx : 0;
+    const int z0 = vb.z * zb;
+    const int z1 = min(z0 + zb, d.nz);
+    liquid_column<S, ZBMAX>(d, in, x, y, z0, z1);
 }
 template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(const __grid_constant__ Dev d) {
@@ -945,13 +950,12 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
 // come in one round of loads, so a thread whose column holds no fluid leaves
 // after one memory latency, and a fluid cell waits on its populations only.
 template <int S, int ZBMAX>
-__device__ __forceinline__ void liquid_column(const Dev &d, int x, int y, int z0, int z1) {
+__device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int y, int z0, int z1) {
     using P = Sto<S>;
     using R = typename P::R;
     static_assert(ZBMAX <= 8, "flags of a column (z1 - z0 <= ZBMAX) are packed into 64 bits");
-    const bool in = x < d.nx;
     const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
-    long long i = (long long)(in ? x : 0) + sy * (y + (long long)d.ny * z0);
+    long long i = (long long)x + sy * (y + (long long)d.ny * z0);
     const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1;
     uint64_t fl = 0;
 #pragma unroll
@@ -1662,6 +1666,18 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
         for (int k = 0; k < 3; ++k) b.v[k] = b.w[k] = b.dv[k] = b.dw[k] = 0.0;
         return;
     }
+    // the update is driven by the mean of this step's and the previous step's
+    // force and torque (the force alone on the first step): near tau = 1/2 a
+    // force that flips sign every step would feed the barely damped BGK modes
+    // of that period through the wall velocity
+    double Fh[3], Th[3];
+    for (int k = 0; k < 3; ++k) {
+        Fh[k] = b.nF ? 0.5 * (b.F[k] + b.Fp[k]) : b.F[k];
+        Th[k] = b.nF ? 0.5 * (b.T[k] + b.Tp[k]) : b.T[k];
+        b.Fp[k] = b.F[k];
+        b.Tp[k] = b.T[k];
+    }
+    b.nF = 1;
     double vol = ((8.0 * b.h[0]) * b.h[1]) * b.h[2];
     double mass = b.dens * vol;
     double I[3] = {(mass / 3.0) * (b.h[1] * b.h[1] + b.h[2] * b.h[2]), (mass / 3.0) * (b.h[0] * b.h[0] + b.h[2] * b.h[2]),
@@ -1669,7 +1685,7 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     double If[3] = {I[0] / b.dens, I[1] / b.dens, I[2] / b.dens};
     double den = mass + VIRTUAL_MASS * vol;
     for (int k = 0; k < 3; ++k) {
-        double num = (b.F[k] + mass * d.grav[k]) + VIRTUAL_MASS * (vol * b.dv[k]);
+        double num = (Fh[k] + mass * d.grav[k]) + VIRTUAL_MASS * (vol * b.dv[k]);
         b.dv[k] = num / den;
         b.v[k] = b.v[k] + b.dv[k];
     }
@@ -1679,7 +1695,7 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     rotation(b.q, R);
     if (base == 2) {
         const double *ax = b.axis;
-        double ta = (b.T[0] * ax[0] + b.T[1] * ax[1]) + b.T[2] * ax[2];
+        double ta = (Th[0] * ax[0] + Th[1] * ax[1]) + Th[2] * ax[2];
         double ab[3];
         for (int k = 0; k < 3; ++k) ab[k] = (R[0 * 3 + k] * ax[0] + R[1 * 3 + k] * ax[1]) + R[2 * 3 + k] * ax[2];
         double Ia = (ab[0] * ab[0] * I[0] + ab[1] * ab[1] * I[1]) + ab[2] * ab[2] * I[2];
@@ -1692,7 +1708,7 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
         double wb[3], tb[3], L[3], gy[3];
         for (int k = 0; k < 3; ++k) {
             wb[k] = (R[0 * 3 + k] * b.w[0] + R[1 * 3 + k] * b.w[1]) + R[2 * 3 + k] * b.w[2];
-            tb[k] = (R[0 * 3 + k] * b.T[0] + R[1 * 3 + k] * b.T[1]) + R[2 * 3 + k] * b.T[2];
+            tb[k] = (R[0 * 3 + k] * Th[0] + R[1 * 3 + k] * Th[1]) + R[2 * 3 + k] * Th[2];
             L[k] = I[k] * wb[k];
         }
         gy[0] = wb[1] * L[2] - wb[2] * L[1];
@@ -2034,10 +2050,13 @@ template <int S> struct Launch {
         if (d.nb > 0) k_forces<S><<<dim3(FORCE_BLOCKS, d.nb), dim3(32, 8), 0, st>>>(d);
         mark();
         {
-            dim3 grid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
+            const long long nxy = (long long)d.nx * d.ny;
+            dim3 grid((unsigned)((nxy + BULK_THREADS - 1) / BULK_THREADS), 1, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
             if constexpr (S != 0) {
-                dim3 pgrid(grid.x, grid.y, (d.nz + LBMFS_BULK_PIPE_ZB - 1) / LBMFS_BULK_PIPE_ZB);
-                if (d.bulk == BULK_TMA) k_liquid_tma<S><<<grid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
+                // the staged variants tile rows: (ceil(nx / BULK_THREADS), ny, z-blocks)
+                dim3 rgrid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
+                dim3 pgrid(rgrid.x, rgrid.y, (d.nz + LBMFS_BULK_PIPE_ZB - 1) / LBMFS_BULK_PIPE_ZB);
+                if (d.bulk == BULK_TMA) k_liquid_tma<S><<<rgrid, BULK_THREADS, 128 + 2 * Stage<S>::BYTES, st>>>(d);
                 else if (d.bulk == BULK_PIPE) k_liquid_pipe<S><<<pgrid, BULK_THREADS, 0, st>>>(d);
                 else k_liquid<S><<<grid, BULK_THREADS, 0, st>>>(d);
             } else {
@@ -2061,7 +2080,7 @@ template <int S> struct Launch {
         mark();
         k_conv_finish<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
-        if (d.nb > 0) k_bodies<<<d.nb, 32, 0, st>>>(d);
+        if (d.nb > 0) launch_bodies(d, st);
         mark();
         if (d.nb > 0) k_remap_cover<S><<<dim3(FORCE_BLOCKS, d.nb), 256, 0, st>>>(d);
         mark();
@@ -2106,7 +2125,7 @@ template <int S> struct BatchStep {
         mark();
         batch_launch<BkConvFinish<S>>(b, SH_LIST, LIST_THREADS, st);
         mark();
-        batch_launch<BkBodies>(b, SH_BODY, 32, st);
+        launch_bodies_batch(b, st);
         mark();
         batch_launch<BkRemapCover<S>>(b, SH_FORCE, 256, st);
         mark();

@@ -366,6 +366,12 @@ class _Handle:
     def stats(self) -> dict:
         return lbm_fs_stats(self.h)
 
+    def flags(self) -> np.ndarray:
+        """The cell classes alone (one byte per cell)."""
+        out = np.zeros(self.n, np.uint8)
+        lbm_fs_read_fields(self.h, FIELD_FLAGS, [out.ctypes.data, None, None, None, None, None], False)
+        return out
+
     def fields(self, want_f: bool = False, on_device: bool = False) -> dict:
         n = self.n
         mask = FIELD_FLAGS | FIELD_FILL | FIELD_MASS | FIELD_RHO | FIELD_VEL | (FIELD_F if want_f else 0)
