@@ -606,8 +606,9 @@ __device__ __forceinline__ VB vb_own() { return VB{blockIdx.x, blockIdx.y, block
     for (uint32_t it_##var = vb.x * blockDim.x + threadIdx.x; it_##var < n_##var;                              \
          it_##var += vb.nx * blockDim.x)
 
-// neighbour-obstacle bit: set when any of the 18 neighbours is an obstacle or
-// lies beyond a wall face (the bulk kernel then takes its general path)
+// neighbour-obstacle bit: set when any of the 18 neighbours is an obstacle
+// (the bulk kernel then takes its general path; walls and periodic seams are
+// recognised from the cell's coordinates)
 __device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
     int x, y, z;
     coords(d, i, x, y, z);
@@ -615,7 +616,7 @@ __device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
 #pragma unroll 1
     for (int q = 1; q < Q; ++q) {
         int c = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
-        nb = nb || c == CL_O || c == CL_WALL;
+        nb = nb || c == CL_O;
     }
     d.flags[i] = (uint8_t)((d.flags[i] & CL_MASK) | (nb ? NB_OBST : 0));
 }
@@ -629,7 +630,7 @@ __global__ void k_nb_all(Dev d) {
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         int c = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
-        nb = nb || c == CL_O || c == CL_WALL;
+        nb = nb || c == CL_O;
     }
     d.flags[i] = (uint8_t)((d.flags[i] & CL_MASK) | (nb ? NB_OBST : 0));
 }
@@ -974,6 +975,16 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
             // touches gas: plain pull from the 18 neighbours
 #pragma unroll
             for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            fp[0] = P::ld(d.fsrc, 0, i, N);
+        } else if (c == CL_L) {
+            // on a face of the grid, no obstacle neighbour: pull across
+            // periodic seams; a resting wall returns the cell's own opposite
+            // population (Eq. noslip with u_w = 0)
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                fp[q] = si >= 0 ? P::ld(d.fsrc, q, si, N) : P::ld(d.fsrc, opp(q), i, N);
+            }
             fp[0] = P::ld(d.fsrc, 0, i, N);
         } else {
             gather_general<S>(d, x, y, z, i, fp);
