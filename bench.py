@@ -178,6 +178,81 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
                                                                + st["wall_source"])) / st["mass0"])
 
 
+def run_batch(scenes, storage, steps, warmup, kernel_steps, separate_steps=20, barrier=None):
+    """The batched form on many tanks (one launch per kernel for all tanks):
+    autotuned tiling, CUDA-event time of `steps` steps on the batch's stream,
+    bytes from the fluid cells of every tank; for comparison, the same tanks
+    as separate handles stepped one after another on the same stream."""
+    import torch
+
+    from paper_1201_0351_gb300 import lbm_fs
+
+    bt = lbm_fs.Batch(scenes, storage=storage, use_graphs=True)
+    bt.step(warmup)
+    bt.sync()
+    cfg = bt.autotune()
+    bt.step(2)
+    bt.sync()
+
+    def counts():
+        liq = itf = 0
+        for t in bt.tanks:
+            fl = t.flags()
+            liq += int((fl == 1).sum())
+            itf += int((fl == 2).sum())
+        return liq, itf
+
+    liq0, if0 = counts()
+    launches0, _ = bt.launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    start.record(bt.stream)
+    bt.step(steps)
+    end.record(bt.stream)
+    end.synchronize()
+    if barrier:
+        barrier()
+    ms = start.elapsed_time(end)
+    launches = bt.launches()[0] - launches0
+    liq1, if1 = counts()
+    kt = bt.kernel_times(kernel_steps)
+    bt.sync()
+    cells = bt.cells
+    bt.close()
+    del bt
+    torch.cuda.empty_cache()
+    n_liq, n_if = 0.5 * (liq0 + liq1), 0.5 * (if0 + if1)
+    b_fluid = BYTES_PER_FLUID[storage]
+    step_bytes = (n_liq + n_if) * b_fluid + cells + n_if * 24
+    liquid_bytes = n_liq * b_fluid + cells
+    liquid_ms = kt["liquid"] / kernel_steps
+    # the same tanks as separate handles (each with its own captured graphs)
+    sims = [lbm_fs.Simulation(sc, storage=storage) for sc in scenes]
+    for sim in sims:
+        sim.step(2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    start.record(stream)
+    for _ in range(separate_steps):
+        for sim in sims:
+            sim.step(1)
+    end.record(stream)
+    end.synchronize()
+    ms_sep = start.elapsed_time(end) / separate_steps
+    for sim in sims:
+        sim.close()
+    del sims
+    torch.cuda.empty_cache()
+    total_k = sum(kt.values())
+    return dict(storage=storage, tanks=len(scenes), cells=cells, ms_total=ms, ms_per_step=ms / steps,
+                mlups=cells * steps / (ms * 1e-3) / 1e6, step_gbs=step_bytes / (ms / steps * 1e-3) / 1e9,
+                liquid_ms=liquid_ms, liquid_bytes=liquid_bytes, liquid_gbs=liquid_bytes / (liquid_ms * 1e-3) / 1e9,
+                kernel_share={k: v / total_k for k, v in kt.items() if total_k > 0}, launches=launches,
+                autotune=cfg, separate_ms_per_step=ms_sep, mass_resid=None)
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -262,6 +337,7 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=0, help="steps of the FP64 variant (default steps // 10)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tank sweep")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end run (default: the workload's job length)")
     args = ap.parse_args()
     ws, rank, local = dist_info()
@@ -303,6 +379,12 @@ def main():
         variants["f16s"] = run_storage(sc, "f16s", args.steps, max(args.warmup, 3), 5, barrier=barrier)
         f64_steps = args.f64_steps or max(3, args.steps // 10)
         variants["f64"] = run_storage(sc, "f64", f64_steps, 3, 2, barrier=barrier)
+    batch = None
+    if not args.no_variants and not args.no_batch:
+        from paper_1201_0351_gb300 import inputs
+
+        batch = run_batch(inputs.batched_sweep_tanks(64), "f16s", args.steps, max(args.warmup, 3), 5,
+                          barrier=barrier)
     ms = main_run["ms_total"]
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -332,6 +414,17 @@ def main():
                                                "mass_resid")} | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k]}
                      for k, v in variants.items()},
     }
+    if batch is not None:
+        line["batch"] = {
+            "workload": "64 tanks of edge 48..112 (seeded), heeled boxes, FP16-shifted storage, one launch per "
+                        "kernel for all tanks", "dtype": DTYPE["f16s"], "cells": batch["cells"],
+            "mlups": batch["mlups"], "ms_per_step": batch["ms_per_step"], "launches": batch["launches"],
+            "roofline": {"bound": "hbm", "kernel": "batched k_liquid", "achieved": batch["liquid_gbs"], "peak": hbm,
+                         "unit": "GB/s", "frac": batch["liquid_gbs"] / hbm,
+                         "algorithmic_bytes_per_launch": batch["liquid_bytes"],
+                         "step_achieved_gbs": batch["step_gbs"], "step_frac": batch["step_gbs"] / hbm},
+            "kernel_share": batch["kernel_share"], "autotune": batch["autotune"],
+            "separate_handles_ms_per_step": batch["separate_ms_per_step"]}
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
