@@ -325,6 +325,23 @@ __device__ __forceinline__ double link_cuw(const Dev &d, const Body &b, int x, i
     return (cx(q) * uw[0] + cy(q) * uw[1]) + cz(q) * uw[2];
 }
 
+// the same in float for the float storages: the body state is rounded once
+// (positions relative to the body centre stay well inside float precision)
+__device__ __forceinline__ float link_cuw_f(const Dev &d, const Body &b, int x, int y, int z, int q) {
+    const int qb = opp(q);
+    float r[3] = {(float)(x - b.o[0]) + (0.5f + 0.5f * cx(qb)), (float)(y - b.o[1]) + (0.5f + 0.5f * cy(qb)),
+                  (float)(z - b.o[2]) + (0.5f + 0.5f * cz(qb))};
+    const int nn[3] = {d.nx, d.ny, d.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (d.periodic & (1u << k)) r[k] -= (float)nn[k] * floorf(r[k] / (float)nn[k] + 0.5f);
+    const float w0 = (float)b.w[0], w1 = (float)b.w[1], w2 = (float)b.w[2];
+    const float u0 = (float)b.v[0] + (w1 * r[2] - w2 * r[1]);
+    const float u1 = (float)b.v[1] + (w2 * r[0] - w0 * r[2]);
+    const float u2 = (float)b.v[2] + (w0 * r[1] - w1 * r[0]);
+    return (cx(q) * u0 + cy(q) * u1) + cz(q) * u2;
+}
+
 // ------------------------------------------------- double arithmetic (Sec. 2.1)
 
 // Eq. equilibrium, c_s^2 = 1/3
@@ -834,21 +851,37 @@ __global__ void __launch_bounds__(256) k_forces(const __grid_constant__ Dev d) {
 
 // Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
 // an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
-// Kept out of line so that the bulk kernel's populations stay in registers.
+// Returns f'_q and the mass the moving wall adds to the cell (the caller sums
+// it per cell for the ledger).  Double arithmetic for the FP64 storage; float
+// for the float storages, whose populations are float anyway (GB300's FP64
+// rate is 1/64 of its FP32 rate).  Kept out of line so that the bulk kernel's
+// populations stay in registers.
+template <class R> struct Bounce {
+    R f, src;
+};
 template <int S>
-__device__ __noinline__ typename Sto<S>::R bounce_back(const Dev &d, int q, long long si, int ns, long long i, int x,
-                                                       int y, int z) {
+__device__ __noinline__ Bounce<typename Sto<S>::R> bounce_back(const Dev &d, int q, long long si, int ns, long long i,
+                                                               int x, int y, int z) {
     using R = typename Sto<S>::R;
-    int qb = opp(q);
-    R own = Sto<S>::ld(d.fsrc, qb, i, d.N);
-    double cuw = 0.0;
-    if (ns == CL_O) cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
-    else if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
-    if (cuw == 0.0) return own;
-    double rho_x = cell_density<S>(d, d.fsrc, i);
-    double src = ((6.0 * wd(q)) * rho_x) * cuw;  // mass the moving wall adds to the liquid cell
-    atomicAdd(&d.ledger[LG_WALL], src);
-    return (R)((double)own + src);
+    const int qb = opp(q);
+    const R own = Sto<S>::ld(d.fsrc, qb, i, d.N);
+    if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
+    if (ns != CL_O) return Bounce<R>{own, R(0)};
+    if constexpr (S == 0) {
+        const double cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
+        if (cuw == 0.0) return Bounce<R>{own, 0.0};
+        const double rho_x = cell_density<S>(d, d.fsrc, i);
+        const double src = ((6.0 * wd(q)) * rho_x) * cuw;
+        return Bounce<R>{own + src, src};
+    } else {
+        const float cuw = link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q);
+        if (cuw == 0.0f) return Bounce<R>{own, 0.0f};
+        float dr = 0.0f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
+        const float src = ((6.0f * wf(q)) * (1.0f + dr)) * cuw;
+        return Bounce<R>{own + src, src};
+    }
 }
 
 // ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
@@ -905,14 +938,21 @@ template <int S>
 __device__ __forceinline__ void gather_general(const Dev &d, int x, int y, int z, long long i,
                                                typename Sto<S>::R *fp) {
     using P = Sto<S>;
+    typename P::R wall = 0;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
         int ns = cls(d, si);
-        if (ns == CL_L || ns == CL_I) fp[q] = P::ld(d.fsrc, q, si, d.N);
-        else fp[q] = bounce_back<S>(d, q, si, ns, i, x, y, z);
+        if (ns == CL_L || ns == CL_I) {
+            fp[q] = P::ld(d.fsrc, q, si, d.N);
+        } else {
+            const auto b = bounce_back<S>(d, q, si, ns, i, x, y, z);
+            fp[q] = b.f;
+            wall += b.src;
+        }
     }
     fp[0] = P::ld(d.fsrc, 0, i, d.N);
+    if (wall != 0) atomicAdd(&d.ledger[LG_WALL], (double)wall);  // mass the moving walls added to the cell
 }
 
 template <int S>
@@ -976,10 +1016,21 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
 #pragma unroll
             for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
             fp[0] = P::ld(d.fsrc, 0, i, N);
+        } else if (c == CL_L && !d.periodic) {
+            // on a face of a grid without periodic axes, no obstacle
+            // neighbour: a source beyond a face is a resting wall, which
+            // returns the cell's own opposite population (Eq. noslip, u_w = 0)
+            const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0,
+                       zh = z == d.nz - 1;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
+                                 (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
+                fp[q] = out ? P::ld(d.fsrc, opp(q), i, N) : P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            }
+            fp[0] = P::ld(d.fsrc, 0, i, N);
         } else if (c == CL_L) {
-            // on a face of the grid, no obstacle neighbour: pull across
-            // periodic seams; a resting wall returns the cell's own opposite
-            // population (Eq. noslip with u_w = 0)
+            // on a face with periodic axes: pull across the seams, walls as above
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
@@ -1380,7 +1431,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                 int ns = cls(d, si);
                 if (ns == CL_WALL || ns == CL_O) {
                     solid |= 1u << q;
-                    float cuw = ns == CL_O ? (float)link_cuw(d, d.bodies[d.bid[si]], x, y, z, q) : 0.0f;
+                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q) : 0.0f;
                     fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
                 } else if (ns == CL_G) {
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
