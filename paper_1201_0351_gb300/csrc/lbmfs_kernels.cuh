@@ -774,27 +774,44 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                     // reduced-precision storage: the link term is split into the
                     // uniform gas-pressure part 2 w_q rho_G (double) and the small
                     // remainder 2 (phi (f_qbar - w_q rho_G) + moving-wall part),
-                    // computed in float from the stored deviations f - w
-                    float phf = (float)phi_x;
-                    float wrg1 = (float)(1.0 - d.rho_g);
-                    float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
-                    float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
-                    float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
-                    float rho_x = -1.0f;
-#pragma unroll 1
+                    // computed in float from the stored deviations f - w.  The
+                    // lever arm r is the cell's, so each part is summed over the
+                    // cell's links first and its torque is r x that sum.
+                    // Directions into body bi: all neighbour classes requested
+                    // at once, then the body ids of the obstacle directions.
+                    unsigned om = 0, lm = 0;
+#pragma unroll
                     for (int q = 1; q < Q; ++q) {
-                        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
-                        int qb = opp(q);
-                        double s0 = 2.0 * (wd(q) * d.rho_g);
+                        const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                        if (si >= 0 && clsv(d, si) == CL_O) om |= 1u << q;
+                    }
+#pragma unroll
+                    for (int q = 1; q < Q; ++q)
+                        if (om & (1u << q))
+                            if (d.bid[nbr(d, x, y, z, -cx(q), -cy(q), -cz(q))] == bi) lm |= 1u << q;
+                    if (!lm) continue;
+                    const float phf = (float)phi_x;
+                    const float wrg1 = (float)(1.0 - d.rho_g);
+                    const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+                    const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
+                    const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
+                    float rho_x = -1.0f;
+                    double sx = 0.0, sy = 0.0, sz = 0.0;  // sum of 2 w_q rho_G c_qbar
+                    float gx = 0.0f, gy = 0.0f, gz = 0.0f, gabs = 0.0f;
+#pragma unroll
+                    for (int q = 1; q < Q; ++q) {
+                        if (!(lm & (1u << q))) continue;
+                        const int qb = opp(q);
+                        const double s0 = 2.0 * (wd(q) * d.rho_g);
                         float gdev = 0.0f;
                         if (cl != CL_G) {
                             // u_w at the link midpoint, r + c_qbar / 2 from the body centre
-                            float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb), pz = rf[2] + 0.5f * cz(qb);
-                            float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
-                            float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
-                            float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
-                            float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+                            const float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb),
+                                        pz = rf[2] + 0.5f * cz(qb);
+                            const float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
+                            const float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
+                            const float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
+                            const float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
                             float C = 0.0f;
                             if (cuw != 0.0f) {
                                 if (rho_x < 0.0f) {
@@ -805,26 +822,24 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                                 }
                                 C = phf * (3.0f * wf(q) * rho_x * cuw);
                             }
-                            float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
+                            const float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
                             gdev = 2.0f * (phf * dev + C);
                         }
-                        // static part in double
-                        if (cx(qb)) acc[0] += cx(qb) * s0;
-                        if (cy(qb)) acc[1] += cy(qb) * s0;
-                        if (cz(qb)) acc[2] += cz(qb) * s0;
-                        acc[3] += s0 * (r[1] * cz(qb) - r[2] * cy(qb));
-                        acc[4] += s0 * (r[2] * cx(qb) - r[0] * cz(qb));
-                        acc[5] += s0 * (r[0] * cy(qb) - r[1] * cx(qb));
-                        // remainder in float
-                        float F0 = cx(qb) * gdev, F1 = cy(qb) * gdev, F2 = cz(qb) * gdev;
-                        acc[0] += (double)F0;
-                        acc[1] += (double)F1;
-                        acc[2] += (double)F2;
-                        acc[3] += (double)(rf[1] * F2 - rf[2] * F1);
-                        acc[4] += (double)(rf[2] * F0 - rf[0] * F2);
-                        acc[5] += (double)(rf[0] * F1 - rf[1] * F0);
-                        acc[6] += fabs(s0 + (double)gdev);
+                        if (cx(qb)) sx += cx(qb) * s0;
+                        if (cy(qb)) sy += cy(qb) * s0;
+                        if (cz(qb)) sz += cz(qb) * s0;
+                        if (cx(qb)) gx += cx(qb) * gdev;
+                        if (cy(qb)) gy += cy(qb) * gdev;
+                        if (cz(qb)) gz += cz(qb) * gdev;
+                        gabs += fabsf((float)s0 + gdev);
                     }
+                    acc[0] += sx + (double)gx;
+                    acc[1] += sy + (double)gy;
+                    acc[2] += sz + (double)gz;
+                    acc[3] += (r[1] * sz - r[2] * sy) + (double)(rf[1] * gz - rf[2] * gy);
+                    acc[4] += (r[2] * sx - r[0] * sz) + (double)(rf[2] * gx - rf[0] * gz);
+                    acc[5] += (r[0] * sy - r[1] * sx) + (double)(rf[0] * gy - rf[1] * gx);
+                    acc[6] += (double)gabs;
                 }
             }
         }
