@@ -167,6 +167,10 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     }
     d.rho_g = p->rho_gas;
     d.eps = p->eps;
+    d.omega_f = (float)d.omega;
+    for (int k = 0; k < 3; ++k) d.a_f[k] = (float)d.a[k];
+    d.drg_f = (float)(d.rho_g - 1.0);
+    d.rg1_f = (float)(1.0 - d.rho_g);
     d.cap = (uint32_t)N;
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
     // bulk-kernel variant (float storages): direct loads by default;

@@ -390,9 +390,9 @@ __device__ __forceinline__ double cell_rho_u(const Dev &d, const void *g, long l
             if (cz(q)) j2 += cz(q) * v;
         }
         float r = 1.0f + dr;
-        u[0] = (double)(j0 / r - (float)d.a[0]);
-        u[1] = (double)(j1 / r - (float)d.a[1]);
-        u[2] = (double)(j2 / r - (float)d.a[2]);
+        u[0] = (double)(j0 / r - d.a_f[0]);
+        u[1] = (double)(j1 / r - d.a_f[1]);
+        u[2] = (double)(j2 / r - d.a_f[2]);
         return 1.0 + (double)dr;
     }
     double f[Q];
@@ -451,8 +451,8 @@ __device__ __forceinline__ float collide_f(const Dev &d, const float *dp, float 
     float inv = 1.0f / rho;
     float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
     float usq = ux * ux + uy * uy + uz * uz;
-    float om = (float)d.omega;
-    float ax = (float)d.a[0], ay = (float)d.a[1], az = (float)d.a[2];
+    float om = d.omega_f;
+    float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
     float ua = ux * ax + uy * ay + uz * az;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -488,8 +488,8 @@ __device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, 
     float inv = 1.0f / rho;
     float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
     float usq = ux * ux + uy * uy + uz * uz;
-    float om = (float)d.omega;
-    float ax = (float)d.a[0], ay = (float)d.a[1], az = (float)d.a[2];
+    float om = d.omega_f;
+    float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
     float ua = ux * ax + uy * ay + uz * az;
     float rest = 0.0f;
 #pragma unroll
@@ -717,6 +717,11 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
         }
     }
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long ik[3] = {0, 0, 0}, it[3] = {0, 0, 0};  // exact gas-pressure sums (float storages)
+    // body state in float for the float storages, rounded once per thread
+    const float of[3] = {(float)b.o[0], (float)b.o[1], (float)b.o[2]};
+    const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
+    const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
     // z-planes over blocks, (x, y) over the block's 32 x 8 threads; only cells
     // next to an obstacle (neighbour-obstacle bit) can hold links
     for (int zz = lo[2] + (int)vb.x; zz < hi[2]; zz += vb.nx) {
@@ -729,11 +734,11 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                 int fb = d.flags[i];
                 int cl = fb & CL_MASK;
                 if (!(fb & NB_OBST) || cl == CL_O) continue;
-                double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
-                double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
-                               min_image(d, (z + 0.5) - b.o[2], 2)};
                 if constexpr (S == 0) {
                     // double, in the order of the plain restatement
+                    const double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
+                    const double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
+                                         min_image(d, (z + 0.5) - b.o[2], 2)};
                     bool have_rho = false;
                     double rho_x = 0.0;
 #pragma unroll 1
@@ -790,19 +795,33 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                         if (om & (1u << q))
                             if (d.bid[nbr(d, x, y, z, -cx(q), -cy(q), -cz(q))] == bi) lm |= 1u << q;
                     if (!lm) continue;
-                    const float phf = (float)phi_x;
-                    const float wrg1 = (float)(1.0 - d.rho_g);
-                    const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
-                    const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
-                    const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
+                    const float phf = cl == CL_L ? 1.0f : (cl == CL_I ? (float)d.phisrc[i] : 0.0f);
+                    const float rg = (float)d.rho_g, wrg1 = d.rg1_f;
+                    // lever arm from the cell centre (minimum image on periodic
+                    // axes): float for the small remainder, and twice the cell
+                    // centre as an integer for the exact gas-pressure part
+                    const int xyz[3] = {x, y, z}, nn[3] = {d.nx, d.ny, d.nz};
+                    float rf[3];
+                    long long c2[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        int xk = xyz[k];
+                        rf[k] = ((float)xk + 0.5f) - of[k];
+                        if (d.periodic & (1u << k)) {
+                            const int sh = (int)floorf(rf[k] / (float)nn[k] + 0.5f);
+                            xk -= sh * nn[k];
+                            rf[k] -= (float)(sh * nn[k]);
+                        }
+                        c2[k] = 2ll * xk + 1;
+                    }
                     float rho_x = -1.0f;
-                    double sx = 0.0, sy = 0.0, sz = 0.0;  // sum of 2 w_q rho_G c_qbar
-                    float gx = 0.0f, gy = 0.0f, gz = 0.0f, gabs = 0.0f;
+                    int kx = 0, ky = 0, kz = 0;  // sum of 36 (2 w_q) c_qbar over the links
+                    float gx = 0.0f, gy = 0.0f, gz = 0.0f, fabs_sum = 0.0f;
 #pragma unroll
                     for (int q = 1; q < Q; ++q) {
                         if (!(lm & (1u << q))) continue;
                         const int qb = opp(q);
-                        const double s0 = 2.0 * (wd(q) * d.rho_g);
+                        const int m36 = q <= 6 ? 4 : 2;  // 36 x 2 w_q
                         float gdev = 0.0f;
                         if (cl != CL_G) {
                             // u_w at the link midpoint, r + c_qbar / 2 from the body centre
@@ -825,44 +844,91 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                             const float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
                             gdev = 2.0f * (phf * dev + C);
                         }
-                        if (cx(qb)) sx += cx(qb) * s0;
-                        if (cy(qb)) sy += cy(qb) * s0;
-                        if (cz(qb)) sz += cz(qb) * s0;
-                        if (cx(qb)) gx += cx(qb) * gdev;
-                        if (cy(qb)) gy += cy(qb) * gdev;
-                        if (cz(qb)) gz += cz(qb) * gdev;
-                        gabs += fabsf((float)s0 + gdev);
+                        if (cx(qb)) {
+                            kx += cx(qb) * m36;
+                            gx += cx(qb) * gdev;
+                        }
+                        if (cy(qb)) {
+                            ky += cy(qb) * m36;
+                            gy += cy(qb) * gdev;
+                        }
+                        if (cz(qb)) {
+                            kz += cz(qb) * m36;
+                            gz += cz(qb) * gdev;
+                        }
+                        fabs_sum += fabsf((float)m36 * (rg * (1.0f / 36.0f)) + gdev);
                     }
-                    acc[0] += sx + (double)gx;
-                    acc[1] += sy + (double)gy;
-                    acc[2] += sz + (double)gz;
-                    acc[3] += (r[1] * sz - r[2] * sy) + (double)(rf[1] * gz - rf[2] * gy);
-                    acc[4] += (r[2] * sx - r[0] * sz) + (double)(rf[2] * gx - rf[0] * gz);
-                    acc[5] += (r[0] * sy - r[1] * sx) + (double)(rf[0] * gy - rf[1] * gx);
-                    acc[6] += (double)gabs;
+                    // remainder: the cell's links in float, cells in double
+                    acc[0] += (double)gx;
+                    acc[1] += (double)gy;
+                    acc[2] += (double)gz;
+                    acc[3] += (double)(rf[1] * gz - rf[2] * gy);
+                    acc[4] += (double)(rf[2] * gx - rf[0] * gz);
+                    acc[5] += (double)(rf[0] * gy - rf[1] * gx);
+                    acc[6] += (double)fabs_sum;
+                    // gas-pressure part (rho_G / 36) K, exactly in integers:
+                    // its torque is (rho_G / 36) (sum c2 x K / 2 - o x sum K)
+                    ik[0] += kx;
+                    ik[1] += ky;
+                    ik[2] += kz;
+                    it[0] += c2[1] * kz - c2[2] * ky;
+                    it[1] += c2[2] * kx - c2[0] * kz;
+                    it[2] += c2[0] * ky - c2[1] * kx;
                 }
             }
         }
     }
-    // deterministic block reduction (fixed shuffle tree, then warps in order)
+    // deterministic block reduction (fixed shuffle tree, then warps in order);
+    // a warp without any link skips the tree (its sums are exact zeros)
     __shared__ double sh[8][7];
     int tid = threadIdx.x + blockDim.x * threadIdx.y;
     int lane = tid & 31, wid = tid >> 5;
+    const bool any = __any_sync(0xffffffffu, acc[6] != 0.0 || acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0);
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
         double v = acc[c];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (any)
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) sh[wid][c] = v;
+    }
+    __shared__ long long shi[8][6];
+    if constexpr (S != 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            long long v = c < 3 ? ik[c] : it[c - 3];
+            if (any)
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) shi[wid][c] = v;
+        }
     }
     __syncthreads();
     if (tid < 7) {
         double v = 0.0;
         for (int w = 0; w < 8; ++w) v += sh[w][tid];
+        if constexpr (S != 0) {
+            if (tid < 6) {
+                long long K[3] = {0, 0, 0}, T2[3] = {0, 0, 0};
+                for (int w = 0; w < 8; ++w)
+                    for (int k = 0; k < 3; ++k) {
+                        K[k] += shi[w][k];
+                        T2[k] += shi[w][3 + k];
+                    }
+                const double g36 = d.rho_g / 36.0;
+                if (tid < 3) {
+                    v += g36 * (double)K[tid];
+                } else {
+                    const int k = tid - 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                    // (sum c2 x K) / 2 - o x sum K, component k
+                    const double ox = b.o[k1] * (double)K[k2] - b.o[k2] * (double)K[k1];
+                    v += g36 * (0.5 * (double)T2[k] - ox);
+                }
+            }
+        }
         d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = v;
     }
 }
 template <int S>
-__global__ void __launch_bounds__(256) k_forces(const __grid_constant__ Dev d) { forces_body<S>(d, vb_own()); }
+__global__ void __launch_bounds__(256, 2) k_forces(const __grid_constant__ Dev d) { forces_body<S>(d, vb_own()); }
 
 // Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
 // an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
@@ -1435,8 +1501,8 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                 if (cz(q)) j2 += cz(q) * fo[q];
             }
             float rx = 1.0f + drx;
-            float ux = j0 / rx - (float)d.a[0], uy = j1 / rx - (float)d.a[1], uz = j2 / rx - (float)d.a[2];
-            float drg = (float)(d.rho_g - 1.0);
+            float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
+            float drg = d.drg_f;
             fp[0] = fo[0];
             unsigned solid = 0;  // directions whose source is an obstacle or a wall
 #pragma unroll
@@ -2068,7 +2134,7 @@ struct BkReset {
         if (threadIdx.x < WL_COUNT) d.cnt[threadIdx.x] = 0;
     }
 };
-template <int S> LBMFS_BATCH_BODY(BkForces, 256, 1, forces_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkForces, 256, 2, forces_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, 8>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, 1, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
