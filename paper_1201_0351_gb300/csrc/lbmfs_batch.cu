@@ -22,7 +22,7 @@ using namespace lbmfs;
 namespace {
 
 constexpr int ZB_DEFAULT = 4;
-constexpr int LIST_CELLS_DEFAULT = 1024;
+constexpr int LIST_CELLS_DEFAULT = 512;
 
 // a group of at most BATCH_TANKS tanks served by the same launches
 struct Chunk {

@@ -72,6 +72,12 @@ constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2
 #ifndef LBMFS_BULK_PIPE_ZB
 #define LBMFS_BULK_PIPE_ZB 16  // z-planes per block of the software-pipelined bulk kernel
 #endif
+#ifndef LBMFS_IFACE_MINB
+#define LBMFS_IFACE_MINB 4  // resident blocks per SM asked of ptxas for the interface kernel (128 registers)
+#endif
+#ifndef LBMFS_IFACE_GRID
+#define LBMFS_IFACE_GRID (16 * 152)  // blocks of the single-tank interface kernel (16 per SM)
+#endif
 #ifndef LBMFS_ST_CS
 #define LBMFS_ST_CS 0      // population stores with the evict-first (streaming) hint
 #endif
@@ -1564,7 +1570,9 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
     }
 }
 template <int S>
-__global__ void __launch_bounds__(128) k_interface(const __grid_constant__ Dev d) { interface_body<S>(d, vb_own()); }
+__global__ void __launch_bounds__(128, LBMFS_IFACE_MINB) k_interface(const __grid_constant__ Dev d) {
+    interface_body<S>(d, vb_own());
+}
 
 // ------------------------------------------------- C3: conversions (Sec. 2.2)
 
@@ -2136,7 +2144,7 @@ struct BkReset {
 };
 template <int S> LBMFS_BATCH_BODY(BkForces, 256, 2, forces_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, 8>(d, vb, zb)))
-template <int S> LBMFS_BATCH_BODY(BkInterface, 128, 1, interface_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkConvInit, LIST_THREADS, 1, conv_init_body<S>(d, vb))
@@ -2207,7 +2215,7 @@ template <int S> struct Launch {
             }
         }
         mark();
-        k_interface<S><<<LIST_BLOCKS * 2, 128, 0, st>>>(d);
+        k_interface<S><<<LBMFS_IFACE_GRID, 128, 0, st>>>(d);
         mark();
         k_conv_filled<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
