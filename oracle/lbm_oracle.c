@@ -89,6 +89,7 @@ struct orc_sim {
     unsigned periodic;
     long n;
     double tau, grav[3], a[3], rho_g, eps;
+    double sigma; /* surface tension (0: none) */
     uint8_t *flag;
     int *body;
     double *f, *fn;     /* [idx*19 + q] at t and t+1 */
@@ -226,6 +227,54 @@ static double fill_seen(const orc_sim *s, long nidx, double own) {
     if (c == IFC) return s->phi[nidx];
     if (c == GAS) return 0.0;
     return own; /* obstacle or outside: zero gradient */
+}
+
+/* fill level of a cell as seen by its own normal estimate: 1 / phi / 0 */
+static double fill_own(const orc_sim *s, long idx) {
+    int c = s->flag[idx];
+    return c == LIQ ? 1.0 : (c == IFC ? s->phi[idx] : 0.0);
+}
+
+/* unit vector of n (zero when n = 0) */
+static void unit_vector(const double n[3], double out[3]) {
+    double len = sqrt((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) out[k] = len > 0.0 ? n[k] / len : 0.0;
+}
+
+/* Sec. 2.2 Laplace pressure: the mean curvature kappa = div(n^)/2 of the
+ * interface at cell (x,y,z), from the unit normals n^ = -grad(phi)/|grad phi|
+ * (the normals of R6, with the same fill-level rules) of its six axis
+ * neighbours by central differences; a neighbour that is an obstacle or lies
+ * beyond a wall takes the cell's own unit normal nc.  A liquid sphere of
+ * radius R has kappa = 1/R. */
+static double curvature(const orc_sim *s, int x, int y, int z, const double nc[3]) {
+    double div = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double comp[2];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            int e[3] = {0, 0, 0};
+            e[k] = sgn ? -1 : 1;
+            long yi = neighbour(s, x, y, z, e[0], e[1], e[2]);
+            int c = class_of(s, yi);
+            if (c == WALL || c == OBS) {
+                comp[sgn] = nc[k];
+                continue;
+            }
+            int yx = (int)(yi % s->nx), yy = (int)((yi / s->nx) % s->ny), yz = (int)(yi / ((long)s->nx * s->ny));
+            double own = fill_own(s, yi), n[3], nh[3];
+            for (int j = 0; j < 3; ++j) {
+                int f[3] = {0, 0, 0};
+                f[j] = 1;
+                double pm = fill_seen(s, neighbour(s, yx, yy, yz, -f[0], -f[1], -f[2]), own);
+                double pp = fill_seen(s, neighbour(s, yx, yy, yz, f[0], f[1], f[2]), own);
+                n[j] = 0.5 * (pm - pp);
+            }
+            unit_vector(n, nh);
+            comp[sgn] = nh[k];
+        }
+        div += comp[0] - comp[1];
+    }
+    return 0.25 * div;
 }
 
 static double liquid_mass(const orc_sim *s) {
@@ -400,6 +449,28 @@ static void stream_collide(orc_sim *s) {
                 int scl[Q];
                 double fp[Q];
                 fp[0] = fo[0];
+                /* interface cells: normal n = -grad(phi) by central differences
+                 * (R6) and the gas density of the boundary condition, raised
+                 * by the Laplace pressure 2 sigma kappa (p = rho / 3) */
+                double n[3] = {0.0, 0.0, 0.0};
+                double rg = s->rho_g;
+                if (cl == IFC) {
+                    double own = s->phi[i];
+                    for (int k = 0; k < 3; ++k) {
+                        int e[3] = {0, 0, 0};
+                        e[k] = 1;
+                        double pm = fill_seen(s, neighbour(s, x, y, z, -e[0], -e[1], -e[2]), own);
+                        double pp = fill_seen(s, neighbour(s, x, y, z, e[0], e[1], e[2]), own);
+                        n[k] = g_mutation == 7 ? 0.5 * (pp - pm) : 0.5 * (pm - pp);
+                    }
+                    if (s->sigma != 0.0) {
+                        double nc[3];
+                        unit_vector(n, nc);
+                        double kappa = curvature(s, x, y, z, nc);
+                        if (g_mutation == 8) kappa = -kappa;
+                        rg = s->rho_g + (6.0 * s->sigma) * kappa;
+                    }
+                }
                 /* C1: stream with bounce-back / reconstruction */
                 for (int q = 1; q < Q; ++q) {
                     int qb = OPP[q];
@@ -419,28 +490,18 @@ static void stream_collide(orc_sim *s) {
                             fp[q] = fo[qb];
                         } else {
                             /* Eq. reconstruct with the cell's own outgoing population */
-                            fp[q] = (feq(q, s->rho_g, ux) + feq(qb, s->rho_g, ux)) - fo[qb];
+                            fp[q] = (feq(q, rg, ux) + feq(qb, rg, ux)) - fo[qb];
                         }
                     } else {
                         fp[q] = s->f[src[q] * Q + q];
                     }
                 }
                 if (cl == IFC) {
-                    /* normal n = -grad(phi), central differences */
-                    double n[3];
-                    double own = s->phi[i];
-                    for (int k = 0; k < 3; ++k) {
-                        int e[3] = {0, 0, 0};
-                        e[k] = 1;
-                        double pm = fill_seen(s, neighbour(s, x, y, z, -e[0], -e[1], -e[2]), own);
-                        double pp = fill_seen(s, neighbour(s, x, y, z, e[0], e[1], e[2]), own);
-                        n[k] = g_mutation == 7 ? 0.5 * (pp - pm) : 0.5 * (pm - pp);
-                    }
                     for (int q = 1; q < Q; ++q) {
                         double cn = (C[q][0] * n[0] + C[q][1] * n[1]) + C[q][2] * n[2];
                         if (cn < -NORMAL_DEADBAND && scl[q] != OBS && scl[q] != WALL) {
                             int qb = OPP[q];
-                            fp[q] = (feq(q, s->rho_g, ux) + feq(qb, s->rho_g, ux)) - fo[qb];
+                            fp[q] = (feq(q, rg, ux) + feq(qb, rg, ux)) - fo[qb];
                         }
                     }
                     /* Sec. 2.2 mass exchange with the neighbour y = x + c_q */
@@ -924,3 +985,5 @@ void orc_force_term(double rho, const double u[3], const double a[3], double out
 }
 
 void orc_set_mutation(int m) { g_mutation = m; }
+
+void orc_set_surface_tension(orc_sim *s, double sigma) { s->sigma = sigma; }

@@ -69,6 +69,9 @@ void orc_force_term(double rho, const double u[3], const double a[3], double out
 /* Test-only deliberate defects (0 = none), used to show that the pins catch
  * plausible mistakes. */
 void orc_set_mutation(int m);
+/* surface tension sigma (lattice units): the gas pressure of the interface
+ * boundary condition becomes p_G + 2 sigma kappa (Sec. 2.2); 0 disables */
+void orc_set_surface_tension(orc_sim *s, double sigma);
 
 #ifdef __cplusplus
 }

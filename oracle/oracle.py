@@ -62,6 +62,7 @@ def _load():
         lib.orc_feq.argtypes = [C.c_double, D, D]
         lib.orc_force_term.argtypes = [C.c_double, D, D, D]
         lib.orc_set_mutation.argtypes = [I]
+        lib.orc_set_surface_tension.argtypes = [P, C.c_double]
         _lib = lib
         return lib
 
@@ -117,6 +118,9 @@ class OracleSim:
                                 None if self._vel is None else _dp(self._vel))
         if not self.h:
             raise ValueError("oracle rejected the scenario")
+        sigma = float(getattr(sc, "sigma", 0.0) or 0.0)
+        if sigma:
+            lib.orc_set_surface_tension(self.h, sigma)
         for b in sc.boxes:
             self.add_box(b)
 

@@ -27,7 +27,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Callable, List, Optional
+from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
@@ -95,6 +95,7 @@ class Scenario:
     boxes: List[Box]
     steps: int
     vel: Optional[np.ndarray] = None  # float64[3N] (xyz per cell) or None = at rest
+    sigma: float = 0.0  # surface tension (Laplace pressure 2 sigma kappa at the interface); 0 = none
 
     @property
     def n_cells(self) -> int:
@@ -359,3 +360,36 @@ def random_box_scene(nx, ny, nz, seed: int, nboxes: int = 1, periodic: int = 0, 
         boxes.append(Box(center=c, half=half, quat=q, density_ratio=dens, vel=vel, omega=om, mode=MODE_FREE))
     return Scenario("random_%dx%dx%d_s%d" % (nx, ny, nz, seed), nx, ny, nz, periodic, tau, (0.0, 0.0, -g),
                     (0.0, 0.0, 0.0), 1.0, 1e-2, flags, fill, rho, boxes, 100)
+
+
+def droplet(n: int = 30, radius: float = 7.0, sigma: float = 4e-3, tau: float = 0.8, bubble: bool = False,
+            seed_offset: Optional[Sequence[float]] = None) -> Scenario:
+    """A liquid sphere of the given radius in gas (or, with bubble=True, a gas
+    sphere in liquid) at the centre of an n^3 closed box, no gravity, density
+    1 everywhere: the interface layer takes the cells whose centres lie within
+    half a cell of the sphere, with fill level clamp(R + 1/2 - r) (liquid side
+    inward); surface tension sigma."""
+    c = np.array([n / 2.0, n / 2.0, n / 2.0]) if seed_offset is None else np.array(seed_offset, float)
+    z, y, x = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5, np.arange(n) + 0.5, indexing="ij")
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    depth = (radius + 0.5 - r) if not bubble else (r - radius + 0.5)  # > 1: liquid, < 0: gas
+    fill = np.clip(depth, 0.0, 1.0)
+    flags = np.where(depth >= 1.0, LIQUID, np.where(depth <= 0.0, GAS, INTERFACE)).astype(np.uint8)
+    # the interface layer must separate liquid from gas along every D3Q19
+    # link: a liquid cell with a gas cell among its 18 neighbours becomes
+    # interface (cells beyond the closed box's walls do not count)
+    fl3 = flags.reshape(n, n, n)
+    pad = np.pad(fl3, 1, constant_values=0)
+    near_gas = np.zeros_like(fl3, dtype=bool)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if abs(dx) + abs(dy) + abs(dz) in (1, 2):
+                    near_gas |= pad[1 + dz:n + 1 + dz, 1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx] == GAS
+    fl3 = np.where((fl3 == LIQUID) & near_gas, INTERFACE, fl3)
+    flags = fl3.reshape(-1)
+    fill = np.where(flags == LIQUID, 1.0, np.where(flags == GAS, 0.0, np.clip(fill.reshape(-1), 0.01, 0.99)))
+    rho = np.ones(n ** 3)
+    name = "%s_%d_R%g" % ("bubble" if bubble else "droplet", n, radius)
+    return Scenario(name, n, n, n, 0, tau, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2, flags,
+                    fill.astype(np.float64), rho, [], 400, sigma=sigma)
