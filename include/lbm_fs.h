@@ -98,6 +98,13 @@ typedef struct {
     void *alloc_ctx;
     void *stream;          /* cudaStream_t for all work; NULL -> legacy default stream */
     int32_t use_graphs;    /* nonzero: steps replay a captured CUDA graph */
+    /* surface tension sigma >= 0 (Sec. 2.2): the gas pressure of the interface
+     * boundary condition becomes p_G + 2 sigma kappa, kappa the mean curvature
+     * div(n^)/2 of the unit normals n^ = -grad(phi)/|grad phi| of the six axis
+     * neighbours (central differences; an obstacle or wall neighbour takes the
+     * cell's own normal), i.e. the reconstruction uses rho_G + 6 sigma kappa.
+     * 0 disables it (no curvature is computed). */
+    double sigma;
 } lbm_fs_params;
 
 typedef struct {

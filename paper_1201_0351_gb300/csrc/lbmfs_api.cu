@@ -125,6 +125,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     if (!p->init_flags || !p->init_fill || !p->init_rho) return fail(LBM_FS_EINVAL, "init_flags, init_fill and init_rho are required%s");
     if (!(p->rho_gas > 0.0) || !(p->eps >= 0.0)) return fail(LBM_FS_EINVAL, "rho_gas must be positive and eps non-negative%s");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return fail(LBM_FS_EINVAL, "dev_alloc and dev_free go together%s");
+    if (!(p->sigma >= 0.0) || !std::isfinite(p->sigma)) return fail(LBM_FS_EINVAL, "sigma must be finite and >= 0%s");
     double proj = 0.0;
     for (int k = 0; k < 3; ++k) {
         double a = fabs(p->gravity[k] + p->body_accel[k]);
@@ -171,6 +172,8 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     for (int k = 0; k < 3; ++k) d.a_f[k] = (float)d.a[k];
     d.drg_f = (float)(d.rho_g - 1.0);
     d.rg1_f = (float)(1.0 - d.rho_g);
+    d.sigma = p->sigma;
+    d.sigma_f = (float)p->sigma;
     d.cap = (uint32_t)N;
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
     // bulk-kernel variant (float storages): direct loads by default;

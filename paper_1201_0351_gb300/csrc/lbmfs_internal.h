@@ -72,6 +72,8 @@ struct Dev {
     // float copies for the float storages' arithmetic (rounded once on the
     // host: no per-cell double-to-float conversions on the GPU's FP64 pipe)
     float omega_f, a_f[3], drg_f, rg1_f;  // 1/tau, a, rho_G - 1, 1 - rho_G
+    double sigma;  // surface tension (0: none)
+    float sigma_f;
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,

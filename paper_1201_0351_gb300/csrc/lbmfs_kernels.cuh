@@ -1389,6 +1389,76 @@ __device__ __forceinline__ double fill_seen(const Dev &d, long long ni, double o
     return own;
 }
 
+// ---- Sec. 2.2 Laplace pressure: mean curvature kappa = div(n^)/2 at an
+// interface cell from the unit normals of its six axis neighbours (central
+// differences; the normals are those of the reconstruction, -grad(phi) with
+// the same fill-level rules); an obstacle or wall neighbour takes the cell's
+// own unit normal nc.  A liquid sphere of radius R has kappa = 1/R.
+__device__ __forceinline__ void unit_vec_d(const double *n, double *out) {
+    double len = sqrt((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k] = len > 0.0 ? n[k] / len : 0.0;
+}
+__device__ __noinline__ double curvature_d(const Dev &d, int x, int y, int z, double nc0, double nc1, double nc2) {
+    const double nc[3] = {nc0, nc1, nc2};
+    double div = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double comp[2];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int s = sgn ? -1 : 1;
+            const long long yi = nbr(d, x, y, z, k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
+            const int c = cls(d, yi);
+            if (c == CL_WALL || c == CL_O) {
+                comp[sgn] = nc[k];
+                continue;
+            }
+            int yx, yy, yz;
+            coords(d, yi, yx, yy, yz);
+            const double own = c == CL_L ? 1.0 : (c == CL_I ? d.phisrc[yi] : 0.0);
+            double n[3], nh[3];
+            for (int j = 0; j < 3; ++j) {
+                const double pm = fill_seen(d, nbr(d, yx, yy, yz, j == 0 ? -1 : 0, j == 1 ? -1 : 0, j == 2 ? -1 : 0), own);
+                const double pp = fill_seen(d, nbr(d, yx, yy, yz, j == 0 ? 1 : 0, j == 1 ? 1 : 0, j == 2 ? 1 : 0), own);
+                n[j] = 0.5 * (pm - pp);
+            }
+            unit_vec_d(n, nh);
+            comp[sgn] = nh[k];
+        }
+        div += comp[0] - comp[1];
+    }
+    return 0.25 * div;
+}
+// the same in float for the float storages
+__device__ __noinline__ float curvature_f(const Dev &d, int x, int y, int z, float nc0, float nc1, float nc2) {
+    const float nc[3] = {nc0, nc1, nc2};
+    float div = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        float comp[2];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int s = sgn ? -1 : 1;
+            const long long yi = nbr(d, x, y, z, k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
+            const int c = cls(d, yi);
+            if (c == CL_WALL || c == CL_O) {
+                comp[sgn] = nc[k];
+                continue;
+            }
+            int yx, yy, yz;
+            coords(d, yi, yx, yy, yz);
+            const double own = c == CL_L ? 1.0 : (c == CL_I ? d.phisrc[yi] : 0.0);
+            float n[3];
+            for (int j = 0; j < 3; ++j) {
+                const float pm = (float)fill_seen(d, nbr(d, yx, yy, yz, j == 0 ? -1 : 0, j == 1 ? -1 : 0, j == 2 ? -1 : 0), own);
+                const float pp = (float)fill_seen(d, nbr(d, yx, yy, yz, j == 0 ? 1 : 0, j == 1 ? 1 : 0, j == 2 ? 1 : 0), own);
+                n[j] = 0.5f * (pm - pp);
+            }
+            const float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+            comp[sgn] = len > 0.0f ? n[k] / len : 0.0f;
+        }
+        div += comp[0] - comp[1];
+    }
+    return 0.25f * div;
+}
+
 // ---- C1 + C2 for interface cells (Sec. 2.2): reconstruction, mass exchange
 template <int S>
 __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
@@ -1436,6 +1506,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                 j2 += cz(q) * fo[q];
             }
             double ux[3] = {j0 / rho_x - d.a[0], j1 / rho_x - d.a[1], j2 / rho_x - d.a[2]};
+            // gas density of the boundary condition, raised by the Laplace pressure
+            double rg = d.rho_g;
+            if (d.sigma != 0.0) {
+                double nc[3];
+                unit_vec_d(nv, nc);
+                rg = d.rho_g + (6.0 * d.sigma) * curvature_d(d, x, y, z, nc[0], nc[1], nc[2]);
+            }
             fp[0] = fo[0];
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -1444,7 +1521,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                     double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q) : 0.0;
                     fp[q] = fo[qb] + ((6.0 * wd(q)) * rho_x) * cuw;
                 } else if (scl[q] == CL_G) {
-                    fp[q] = (feq_d(q, d.rho_g, ux) + feq_d(qb, d.rho_g, ux)) - fo[qb];
+                    fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
                 } else {
                     fp[q] = P::ld(d.fsrc, q, src[q], N);
                 }
@@ -1454,7 +1531,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                 double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
                 if (cn < -NORMAL_DEADBAND && scl[q] != CL_O && scl[q] != CL_WALL) {
                     int qb = opp(q);
-                    fp[q] = (feq_d(q, d.rho_g, ux) + feq_d(qb, d.rho_g, ux)) - fo[qb];
+                    fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
                 }
             }
             double dm = 0.0;
@@ -1509,6 +1586,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             float rx = 1.0f + drx;
             float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
             float drg = d.drg_f;
+            if (d.sigma != 0.0) {
+                // gas density raised by the Laplace pressure
+                const float len = sqrtf((nv0 * nv0 + nv1 * nv1) + nv2 * nv2);
+                const float nu0 = len > 0.0f ? nv0 / len : 0.0f, nu1 = len > 0.0f ? nv1 / len : 0.0f,
+                            nu2 = len > 0.0f ? nv2 / len : 0.0f;
+                drg = d.drg_f + (6.0f * d.sigma_f) * curvature_f(d, x, y, z, nu0, nu1, nu2);
+            }
             fp[0] = fo[0];
             unsigned solid = 0;  // directions whose source is an obstacle or a wall
 #pragma unroll

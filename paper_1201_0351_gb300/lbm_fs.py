@@ -34,7 +34,7 @@ class lbm_fs_params(C.Structure):
                 ("init_flags", C.c_void_p), ("init_fill", C.c_void_p), ("init_rho", C.c_void_p),
                 ("init_vel", C.c_void_p), ("init_on_device", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("use_graphs", C.c_int32)]
+                ("stream", C.c_void_p), ("use_graphs", C.c_int32), ("sigma", C.c_double)]
 
 
 class lbm_fs_box(C.Structure):
@@ -345,6 +345,7 @@ def scenario_params(sc, storage: str, stream: int, use_graphs: bool, alloc=None,
         p.dev_alloc, p.dev_free = alloc.c_alloc, alloc.c_free
     p.stream = stream
     p.use_graphs = 1 if use_graphs else 0
+    p.sigma = float(getattr(sc, "sigma", 0.0) or 0.0)
     return p
 
 

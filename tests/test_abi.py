@@ -54,7 +54,8 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(tau=0.5), dict(tau=0.4), dict(nx=0), dict(storage=7), dict(rho_gas=0.0),
-                                 dict(eps=-1.0), dict(gravity=(0.0, 0.0, -0.05)), dict(init_flags=None)])
+                                 dict(eps=-1.0), dict(gravity=(0.0, 0.0, -0.05)), dict(init_flags=None),
+                                 dict(sigma=-1e-3), dict(sigma=float("inf"))])
 def test_invalid_parameters_rejected_before_allocation(bad):
     p, keep = _params(**bad)
     with pytest.raises(lbm_fs.LbmFsError) as e:
