@@ -51,6 +51,7 @@ lbm_fs_status read_status(lbm_fs *h) {
     if (st & ST_TIMEOUT) return fail(LBM_FS_ETIMEOUT, "a bounded wait for staged rows gave up%s");
     if (st & ST_NONFINITE) return fail(LBM_FS_EUNSTABLE, "non-finite or non-positive density in a fluid cell%s");
     if (st & ST_LIQUID_GAS) return fail(LBM_FS_EUNSTABLE, "a liquid cell touched a gas cell (open interface layer)%s");
+    if (st & ST_CONTACT) return fail(LBM_FS_EUNSTABLE, "a moving body reached a domain wall (body-wall contact is not modelled)%s");
     return LBM_FS_OK;
 }
 

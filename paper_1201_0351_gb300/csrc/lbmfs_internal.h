@@ -29,7 +29,7 @@ enum : uint8_t {
     MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_PEND = 32, MK_FRESH = 64
 };
 // sticky device status bits
-enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEOUT = 8 };
+enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEOUT = 8, ST_CONTACT = 16 };
 
 // worklists
 enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_COUNT };

@@ -1973,6 +1973,14 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     double norm = sqrt(((nq[0] * nq[0] + nq[1] * nq[1]) + nq[2] * nq[2]) + nq[3] * nq[3]);
     for (int k = 0; k < 4; ++k) b.q[k] = nq[k] / norm;
     body_bounds(d, b);
+    // a moving box that reaches a wall plane would need a contact model
+    // (the paper's rigid-body engine); report it instead of running on
+    for (int k = 0; k < 3; ++k) {
+        if (d.periodic & (1u << k)) continue;
+        const double e = (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) + fabs(b.R[k * 3 + 2]) * b.h[2];
+        const double n = k == 0 ? d.nx : (k == 1 ? d.ny : d.nz);
+        if (b.o[k] - e < 0.0 || b.o[k] + e > n) atomicOr(d.status, ST_CONTACT);
+    }
 }
 __global__ void k_bodies(const __grid_constant__ Dev d) { bodies_body(d, vb_own()); }
 

@@ -393,3 +393,23 @@ def droplet(n: int = 30, radius: float = 7.0, sigma: float = 4e-3, tau: float = 
     name = "%s_%d_R%g" % ("bubble" if bubble else "droplet", n, radius)
     return Scenario(name, n, n, n, 0, tau, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2, flags,
                     fill.astype(np.float64), rho, [], 400, sigma=sigma)
+
+
+def floating_cubes(steps: int = 40000) -> Scenario:
+    """The floating-cube equilibrium of Sec. 3.2.2: a 130x40x40 basin filled to
+    half height, tau 1/1.9, g 7.5e-4, three 32x16x16 boxes (the 2D cube of side
+    s = 16 extended to 2s along its rolling axis x) of densities 0.75, 0.5 and
+    0.25, free to roll about x only and to translate, placed at the draft of
+    their 2.86 deg initial heel.  Stable heels: atan(1/2) = 26.565 deg for 0.25
+    and 0.75, 45 deg for 0.5."""
+    nx, ny, nz = 130, 40, 40
+    g, eta, s = 7.5e-4, 20.0, 16.0
+    flags, fill, rho = hydrostatic_tank(nx, ny, nz, lambda X, Y: eta, g, 1.0, 0)
+    boxes = []
+    for k, dens in enumerate((0.75, 0.5, 0.25)):
+        heel = 2.86
+        zc = eta + immersed_offset(s, s, math.radians(heel), dens)
+        boxes.append(Box(center=(nx * (2 * k + 1) / 6.0, ny / 2.0, zc), half=(s, s / 2, s / 2), quat=heel_quat(heel),
+                         density_ratio=dens, mode=MODE_ROT_AXIS_ONLY, rot_axis=(1.0, 0.0, 0.0)))
+    return Scenario("floating_cubes_130x40x40", nx, ny, nz, 0, 1.0 / 1.9, (0.0, 0.0, -g), (0.0, 0.0, 0.0), 1.0, 1e-2,
+                    flags, fill, rho, boxes, steps)

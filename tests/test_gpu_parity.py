@@ -181,3 +181,25 @@ def test_bulk_kernel_variants_match_plain_kernel(storage, variant, dims, monkeyp
     assert np.array_equal(out[0][0]["flags"], out[1][0]["flags"])
     assert np.array_equal(out[0][0]["f"], out[1][0]["f"])
     assert np.array_equal(out[0][1]["F"], out[1][1]["F"])
+
+
+def test_box_reaching_a_wall_is_reported():
+    """A free box coasting through an all-gas tank (uniform gas pressure, no
+    net force) reaches the far wall: the library stops with a contact error
+    rather than running on without a contact model."""
+    from paper_1201_0351_gb300 import lbm_fs
+
+    n = 40
+    flags = np.full(n * n * n, I.GAS, np.uint8)
+    sc = I.Scenario("coasting_box", n, n, n, 0, 0.7, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2, flags,
+                    np.zeros(n ** 3), np.ones(n ** 3),
+                    [I.Box(center=(20.3, 20.2, 20.1), half=(4.0, 3.0, 3.0), vel=(0.1, 0.0, 0.0), mode=I.MODE_FREE,
+                           density_ratio=0.5)], 200)
+    sim = lbm_fs.Simulation(sc, storage="f32")
+    sim.step(100)
+    sim.sync()  # still 11 cells from the wall
+    sim.step(100)
+    with pytest.raises(lbm_fs.LbmFsError) as e:
+        sim.sync()
+    sim.close()
+    assert e.value.code == lbm_fs.LBM_FS_EUNSTABLE and "wall" in str(e.value)
