@@ -490,23 +490,39 @@ __device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, 
         if (cy(q)) j1 += cy(q) * dp[q];
         if (cz(q)) j2 += cz(q) * dp[q];
     }
-    float rho = 1.0f + dr;
-    float inv = 1.0f / rho;
-    float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
-    float usq = ux * ux + uy * uy + uz * uz;
-    float om = d.omega_f;
-    float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
-    float ua = ux * ax + uy * ay + uz * az;
+    const float rho = 1.0f + dr;
+    const float inv = 1.0f / rho;
+    const float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float om = d.omega_f, om1 = 1.0f - om;
+    const float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
+    const float ua3 = 3.0f * (ux * ax + uy * ay + uz * az);
+    // per weight class: w dr, w rho, 3 w rho
+    const float wdr1 = wf(1) * dr, wr1 = wf(1) * rho, wr13 = 3.0f * wr1;
+    const float wdr2 = wf(7) * dr, wr2 = wf(7) * rho, wr23 = 3.0f * wr2;
     float rest = 0.0f;
+    // opposite directions q, qbar share everything but the sign of c.u and
+    // c.a: f_eq - w = A +- B, force term = C +- D with
+    //   A = w dr + w rho (4.5 (c.u)^2 - 1.5 u.u),  B = 3 w rho c.u,
+    //   C = w rho (9 (c.u)(c.a) - 3 u.a),          D = 3 w rho c.a,
+    // and the relaxed value (1 - omega) dp + omega f_eq + F splits alike
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-        float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
-        float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
-        float deq = wf(q) * (dr + s + dr * s);
-        float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
-        float fq = wf(q) * rho * (3.0f * (ca - ua) + 9.0f * cu * ca);
-        float dn = dp[q] - om * (dp[q] - deq) + fq;
+        const int qb = opp(q);
+        if (qb < q) continue;  // each pair once, from its lower member
+        const bool axis = q <= 6;
+        const float wdr = axis ? wdr1 : wdr2, wr = axis ? wr1 : wr2, wr3 = axis ? wr13 : wr23;
+        const float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
+        const float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
+        const float A = wdr + wr * (4.5f * cu * cu - 1.5f * usq);
+        const float B = wr3 * cu;
+        const float C = wr * (9.0f * cu * ca) - wr * ua3;
+        const float D = wr3 * ca;
+        const float E = om * A + C, G = om * B + D;
+        const float dn = om1 * dp[q] + (E + G);
+        const float dnb = om1 * dp[qb] + (E - G);
         rest += dp[q] - store(q, dn);
+        rest += dp[qb] - store(qb, dnb);
     }
     store(0, dp[0] + rest);
     return rho;
