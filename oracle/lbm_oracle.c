@@ -78,6 +78,7 @@ typedef struct {
     double dv[3], dw[3]; /* last velocity / angular-velocity increments (virtual mass) */
     double Fp[3], Tp[3]; /* the previous step's force and torque */
     int nF;              /* 1 once Fp, Tp hold a step */
+    int shape;           /* 0: box of half extents h; 1: sphere of radius h[0] */
 } body_t;
 
 /* virtual-mass coefficient of the rigid-body update (Schwarz, Kempe and
@@ -90,6 +91,7 @@ struct orc_sim {
     long n;
     double tau, grav[3], a[3], rho_g, eps;
     double sigma; /* surface tension (0: none) */
+    double wall_vel[6][3]; /* velocity of the faces x-, x+, y-, y+, z-, z+ (non-periodic) */
     uint8_t *flag;
     int *body;
     double *f, *fn;     /* [idx*19 + q] at t and t+1 */
@@ -187,12 +189,14 @@ static void rotation(const double q[4], double R[3][3]) {
     R[2][2] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-/* Sec. 2.3: a cell is an obstacle iff its centre lies inside the body. */
+/* Sec. 2.3: a cell is an obstacle iff its centre lies inside the body (a box,
+ * or a sphere of radius h[0]). */
 static int inside(const orc_sim *s, const body_t *b, int x, int y, int z) {
     double R[3][3];
     rotation(b->q, R);
     double d[3] = {min_image(s, (x + 0.5) - b->o[0], 0), min_image(s, (y + 0.5) - b->o[1], 1),
                    min_image(s, (z + 0.5) - b->o[2], 2)};
+    if (b->shape == 1) return ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) < b->h[0] * b->h[0];
     for (int k = 0; k < 3; ++k) {
         double bk = (R[0][k] * d[0] + R[1][k] * d[1]) + R[2][k] * d[2];
         if (!(fabs(bk) < b->h[k])) return 0;
@@ -218,6 +222,21 @@ static void link_wall_velocity(const orc_sim *s, const body_t *b, int x, int y, 
     int qb = OPP[q];
     double p[3] = {(x + 0.5) + 0.5 * C[qb][0], (y + 0.5) + 0.5 * C[qb][1], (z + 0.5) + 0.5 * C[qb][2]};
     body_velocity_at(s, b, p, uw);
+}
+
+/* Eq. noslip at a domain wall: the velocity of the wall face that the link
+ * (x, q) crosses (source x - c_q beyond the grid); a link across an edge takes
+ * the face of the lowest such axis. */
+static void wall_face_velocity(const orc_sim *s, int x, int y, int z, int q, double uw[3]) {
+    int p[3] = {x - C[q][0], y - C[q][1], z - C[q][2]};
+    int nn[3] = {s->nx, s->ny, s->nz};
+    for (int k = 0; k < 3; ++k) {
+        if (s->periodic & (1u << k)) continue;
+        int face = p[k] < 0 ? 2 * k : (p[k] >= nn[k] ? 2 * k + 1 : -1);
+        if (face < 0) continue;
+        for (int j = 0; j < 3; ++j) uw[j] = s->wall_vel[face][j];
+        return;
+    }
 }
 
 /* fill level as seen by the normal estimate of an interface cell */
@@ -340,7 +359,7 @@ void orc_destroy(orc_sim *s) {
 
 int orc_add_box(orc_sim *s, const double center[3], const double half[3], const double quat[4],
                 double density_ratio, const double vel[3], const double omega[3], int mode,
-                const double rot_axis[3], double lin_damping) {
+                const double rot_axis[3], double lin_damping, int shape) {
     if (s->nb == s->cap) {
         s->cap = s->cap ? 2 * s->cap : 4;
         s->b = (body_t *)realloc(s->b, s->cap * sizeof(body_t));
@@ -355,6 +374,7 @@ int orc_add_box(orc_sim *s, const double center[3], const double half[3], const 
     b->dens = density_ratio;
     b->mode = mode;
     b->damp = lin_damping;
+    b->shape = shape;
     int id = s->nb++;
     for (int z = 0; z < s->nz; ++z)
         for (int y = 0; y < s->ny; ++y)
@@ -480,6 +500,7 @@ static void stream_collide(orc_sim *s) {
                         /* Eq. noslip: f'_q = f*_qbar + 2/c_s^2 w_q rho (c_q.u_w) */
                         double uw[3] = {0.0, 0.0, 0.0};
                         if (scl[q] == OBS) link_wall_velocity(s, &s->b[s->body[src[q]]], x, y, z, q, uw);
+                        else wall_face_velocity(s, x, y, z, q, uw);
                         double cuw = (C[q][0] * uw[0] + C[q][1] * uw[1]) + C[q][2] * uw[2];
                         double src_term = ((6.0 * W[q]) * rho_x) * cuw;
                         fp[q] = (g_mutation == 6 ? fo[q] : fo[qb]) + src_term;
@@ -697,11 +718,18 @@ static void bodies_step(orc_sim *s) {
             b->Tp[k] = b->T[k];
         }
         b->nF = 1;
-        double vol = ((8.0 * b->h[0]) * b->h[1]) * b->h[2];
-        double mass = b->dens * vol;
-        double I[3] = {(mass / 3.0) * (b->h[1] * b->h[1] + b->h[2] * b->h[2]),
-                       (mass / 3.0) * (b->h[0] * b->h[0] + b->h[2] * b->h[2]),
-                       (mass / 3.0) * (b->h[0] * b->h[0] + b->h[1] * b->h[1])};
+        double vol, mass, I[3];
+        if (b->shape == 1) { /* sphere: V = 4/3 pi r^3, I = 2/5 m r^2 */
+            vol = 4.1887902047863905 * ((b->h[0] * b->h[0]) * b->h[0]);
+            mass = b->dens * vol;
+            I[0] = I[1] = I[2] = (0.4 * mass) * (b->h[0] * b->h[0]);
+        } else {
+            vol = ((8.0 * b->h[0]) * b->h[1]) * b->h[2];
+            mass = b->dens * vol;
+            I[0] = (mass / 3.0) * (b->h[1] * b->h[1] + b->h[2] * b->h[2]);
+            I[1] = (mass / 3.0) * (b->h[0] * b->h[0] + b->h[2] * b->h[2]);
+            I[2] = (mass / 3.0) * (b->h[0] * b->h[0] + b->h[1] * b->h[1]);
+        }
         double If[3] = {I[0] / b->dens, I[1] / b->dens, I[2] / b->dens}; /* inertia of the displaced liquid */
         double den = mass + VIRTUAL_MASS * vol;
         for (int k = 0; k < 3; ++k) {
@@ -987,3 +1015,8 @@ void orc_force_term(double rho, const double u[3], const double a[3], double out
 void orc_set_mutation(int m) { g_mutation = m; }
 
 void orc_set_surface_tension(orc_sim *s, double sigma) { s->sigma = sigma; }
+
+void orc_set_wall_velocity(orc_sim *s, const double v[18]) {
+    for (int f = 0; f < 6; ++f)
+        for (int j = 0; j < 3; ++j) s->wall_vel[f][j] = v[3 * f + j];
+}

@@ -40,7 +40,7 @@ void orc_destroy(orc_sim *s);
 int orc_add_box(orc_sim *s, const double center[3], const double half[3],
                 const double quat[4], double density_ratio, const double vel[3],
                 const double omega[3], int mode, const double rot_axis[3],
-                double lin_damping);
+                double lin_damping, int shape); /* shape 0: box; 1: sphere of radius half[0] */
 int orc_step(orc_sim *s, int nsteps);
 /* momentum exchange (force, torque) on every body from the current state,
  * without advancing time */
@@ -72,6 +72,9 @@ void orc_set_mutation(int m);
 /* surface tension sigma (lattice units): the gas pressure of the interface
  * boundary condition becomes p_G + 2 sigma kappa (Sec. 2.2); 0 disables */
 void orc_set_surface_tension(orc_sim *s, double sigma);
+/* velocities of the wall faces x-, x+, y-, y+, z-, z+ (3 each; Eq. noslip
+ * with u_w at domain walls); zero by default */
+void orc_set_wall_velocity(orc_sim *s, const double v[18]);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,7 @@ def _load():
                                    C.POINTER(C.c_uint8), D, D, D]
         lib.orc_destroy.argtypes = [P]
         lib.orc_add_box.restype = I
-        lib.orc_add_box.argtypes = [P, D, D, D, C.c_double, D, D, I, D, C.c_double]
+        lib.orc_add_box.argtypes = [P, D, D, D, C.c_double, D, D, I, D, C.c_double, I]
         lib.orc_step.restype = I
         lib.orc_step.argtypes = [P, I]
         lib.orc_compute_forces.argtypes = [P]
@@ -63,6 +63,7 @@ def _load():
         lib.orc_force_term.argtypes = [C.c_double, D, D, D]
         lib.orc_set_mutation.argtypes = [I]
         lib.orc_set_surface_tension.argtypes = [P, C.c_double]
+        lib.orc_set_wall_velocity.argtypes = [P, D]
         _lib = lib
         return lib
 
@@ -121,12 +122,17 @@ class OracleSim:
         sigma = float(getattr(sc, "sigma", 0.0) or 0.0)
         if sigma:
             lib.orc_set_surface_tension(self.h, sigma)
+        wall_vel = getattr(sc, "wall_vel", None)
+        if wall_vel is not None:
+            self._wv = np.ascontiguousarray(np.asarray(wall_vel, dtype=np.float64).reshape(18))
+            lib.orc_set_wall_velocity(self.h, _dp(self._wv))
         for b in sc.boxes:
             self.add_box(b)
 
     def add_box(self, b):
         return self.lib.orc_add_box(self.h, _d3(b.center), _d3(b.half), _d3(b.quat, 4), b.density_ratio,
-                                    _d3(b.vel), _d3(b.omega), b.mode, _d3(b.rot_axis), b.lin_damping)
+                                    _d3(b.vel), _d3(b.omega), b.mode, _d3(b.rot_axis), b.lin_damping,
+                                    int(getattr(b, "shape", 0)))
 
     def __del__(self):
         if getattr(self, "h", None):

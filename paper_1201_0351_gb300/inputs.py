@@ -37,6 +37,7 @@ INTERFACE = 2
 GAS = 4
 
 # Box motion modes (input encoding).
+SHAPE_BOX, SHAPE_SPHERE = 0, 1
 MODE_FIXED = 0
 MODE_FREE = 1
 MODE_ROT_AXIS_ONLY = 2
@@ -75,6 +76,7 @@ class Box:
     mode: int = MODE_FIXED
     rot_axis: tuple = (1.0, 0.0, 0.0)
     lin_damping: float = 0.0
+    shape: int = 0  # SHAPE_BOX, or SHAPE_SPHERE of radius half[0]
 
 
 @dataclasses.dataclass
@@ -96,6 +98,7 @@ class Scenario:
     steps: int
     vel: Optional[np.ndarray] = None  # float64[3N] (xyz per cell) or None = at rest
     sigma: float = 0.0  # surface tension (Laplace pressure 2 sigma kappa at the interface); 0 = none
+    wall_vel: Optional[tuple] = None  # 18 floats: velocity of the faces x-, x+, y-, y+, z-, z+; None = at rest
 
     @property
     def n_cells(self) -> int:
