@@ -106,6 +106,12 @@ typedef struct {
      * cell's own normal), i.e. the reconstruction uses rho_G + 6 sigma kappa.
      * 0 disables it (no curvature is computed). */
     double sigma;
+    /* velocity of each non-periodic face, x-, x+, y-, y+, z-, z+ (Eq. noslip
+     * with u_w: a link whose source lies beyond the face takes
+     * f*_qbar + 6 w_q rho (c_q . u_w); a link across an edge takes the face of
+     * its lowest axis); all zero: resting walls.  The mass a moving wall adds
+     * to liquid cells is booked in lbm_fs_stats_t.wall_source. */
+    double wall_vel[6][3];
 } lbm_fs_params;
 
 typedef struct {
@@ -118,6 +124,8 @@ typedef struct {
     int32_t mode;          /* LBM_FS_MODE_* */
     double rot_axis[3];    /* unit axis (world) for LBM_FS_MODE_ROT_AXIS_ONLY */
     double lin_damping;    /* for LBM_FS_MODE_DAMP_TRANSLATION */
+    int32_t shape;         /* 0: box of half extents half; 1: sphere of radius half[0]
+                              (volume 4/3 pi r^3, inertia 2/5 m r^2; Sec. 3.2.1) */
 } lbm_fs_box;
 
 typedef struct {

@@ -127,6 +127,9 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     if (!(p->rho_gas > 0.0) || !(p->eps >= 0.0)) return fail(LBM_FS_EINVAL, "rho_gas must be positive and eps non-negative%s");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return fail(LBM_FS_EINVAL, "dev_alloc and dev_free go together%s");
     if (!(p->sigma >= 0.0) || !std::isfinite(p->sigma)) return fail(LBM_FS_EINVAL, "sigma must be finite and >= 0%s");
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(p->wall_vel[f][k])) return fail(LBM_FS_EINVAL, "non-finite wall velocity%s");
     double proj = 0.0;
     for (int k = 0; k < 3; ++k) {
         double a = fabs(p->gravity[k] + p->body_accel[k]);
@@ -211,9 +214,15 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.rrho = (double *)h->alloc(N * 8);
     d.rphi = (double *)h->alloc(N * 8);
     d.red = (double *)h->alloc(sizeof(double) * LIST_BLOCKS);
+    double *wallv = (double *)h->alloc(sizeof(double) * 18);
+    d.wallv = wallv;
     for (void *ptr : h->allocs)
         if (!ptr) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
-    if (h->allocs.size() != 17 + WL_COUNT) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
+    if (h->allocs.size() != 18 + WL_COUNT) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
+    d.walls_move = 0;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k)
+            if (p->wall_vel[f][k] != 0.0 && !(d.periodic & (1u << (f / 2)))) d.walls_move = 1;
     cudaStream_t st = h->st;
 #define CKB(call)                                                   \
     do {                                                            \
@@ -230,6 +239,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     CKB(cudaMemsetAsync(d.ledger, 0, sizeof(double) * LG_COUNT, st));
     CKB(cudaMemsetAsync(d.status, 0, 4, st));
     CKB(cudaMemsetAsync(d.part, 0, sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7, st));
+    CKB(cudaMemcpyAsync(wallv, &p->wall_vel[0][0], sizeof(double) * 18, cudaMemcpyHostToDevice, st));
     h->d[0] = d;
     h->d[1] = d;
     set_grids(h, fA, fB, pA, pB);
@@ -286,6 +296,7 @@ lbm_fs_status lbm_fs_add_box(lbm_fs *h, const lbm_fs_box *b, int32_t *out_id) {
     if (!(b->density_ratio > 0.0)) return fail(LBM_FS_EINVAL, "density_ratio must be positive%s");
     int base = b->mode & 0xff;
     if (base > 2 || (b->mode & ~0x1ff)) return fail(LBM_FS_EINVAL, "unknown mode%s");
+    if (b->shape != 0 && b->shape != 1) return fail(LBM_FS_EINVAL, "unknown shape%s");
     Body hb;
     memset(&hb, 0, sizeof hb);
     for (int k = 0; k < 3; ++k) {
@@ -299,6 +310,7 @@ lbm_fs_status lbm_fs_add_box(lbm_fs *h, const lbm_fs_box *b, int32_t *out_id) {
     hb.dens = b->density_ratio;
     hb.damp = b->lin_damping;
     hb.mode = b->mode;
+    hb.shape = b->shape;
     int id = h->nb;
     cudaStream_t st = h->st;
     CK(cudaMemcpyAsync(h->d[0].bodies + id, &hb, sizeof hb, cudaMemcpyHostToDevice, st));

@@ -43,7 +43,7 @@ struct Body {
     double Fp[3], Tp[3];  // the previous step's force and torque (rigid-body update)
     int nF, pad2;         // 1 once Fp, Tp hold a step
     double R[9];        // rotation of q (row-major), recomputed with the pose
-    int mode, pad;
+    int mode, shape;  // shape 0: box of half extents h; 1: sphere of radius h[0]
     int lo[3], hi[3];   // cells that may be inside at the current pose, [lo, hi)
     int plo[3], phi[3]; // the same at the previous pose
 };
@@ -74,6 +74,8 @@ struct Dev {
     float omega_f, a_f[3], drg_f, rg1_f;  // 1/tau, a, rho_G - 1, 1 - rho_G
     double sigma;  // surface tension (0: none)
     float sigma_f;
+    int walls_move;       // nonzero: some non-periodic face moves
+    const double *wallv;  // 6 x 3 face velocities (x-, x+, y-, y+, z-, z+)
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,

@@ -298,16 +298,42 @@ __device__ __forceinline__ void rotation(const double *q, double *R) {
     R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-// Sec. 2.3: cell centre strictly inside the box
+// Sec. 2.3: cell centre strictly inside the body (box, or sphere of radius
+// h[0]); products and sums rounded one by one (no fused multiply-add) so that
+// every storage classifies a centre on the surface the same way
 __device__ __forceinline__ bool inside(const Dev &d, const Body &b, int x, int y, int z) {
     double dd[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
                     min_image(d, (z + 0.5) - b.o[2], 2)};
+    if (b.shape == 1)
+        return __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2])) <
+               __dmul_rn(b.h[0], b.h[0]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double bk = (b.R[0 * 3 + k] * dd[0] + b.R[1 * 3 + k] * dd[1]) + b.R[2 * 3 + k] * dd[2];
+        double bk = __dadd_rn(__dadd_rn(__dmul_rn(b.R[0 * 3 + k], dd[0]), __dmul_rn(b.R[1 * 3 + k], dd[1])),
+                              __dmul_rn(b.R[2 * 3 + k], dd[2]));
         if (!(fabs(bk) < b.h[k])) return false;
     }
     return true;
+}
+
+// Eq. noslip at a domain wall: c_q . u_w with u_w the velocity of the face
+// that the link (x, q) crosses (source beyond the grid); a link across an edge
+// takes the face of its lowest axis
+__device__ __forceinline__ int wall_face(const Dev &d, int x, int y, int z, int q) {
+    const int p[3] = {x - cx(q), y - cy(q), z - cz(q)}, nn[3] = {d.nx, d.ny, d.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d.periodic & (1u << k)) continue;
+        if (p[k] < 0) return 2 * k;
+        if (p[k] >= nn[k]) return 2 * k + 1;
+    }
+    return -1;
+}
+__device__ __forceinline__ double wall_cuw(const Dev &d, int x, int y, int z, int q) {
+    const int f = wall_face(d, x, y, z, q);
+    if (f < 0) return 0.0;
+    const double *u = d.wallv + 3 * f;
+    return (cx(q) * u[0] + cy(q) * u[1]) + cz(q) * u[2];
 }
 
 __device__ __forceinline__ void body_velocity_at(const Dev &d, const Body &b, const double *p, double *uw) {
@@ -572,7 +598,8 @@ __device__ void body_bounds(const Dev &d, Body &b) {
     rotation(b.q, b.R);
     int n[3] = {d.nx, d.ny, d.nz};
     for (int k = 0; k < 3; ++k) {
-        double e = (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) + fabs(b.R[k * 3 + 2]) * b.h[2];
+        double e = b.shape == 1 ? b.h[0]
+                                : (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) + fabs(b.R[k * 3 + 2]) * b.h[2];
         int lo = (int)floor(b.o[k] - e) - 1;
         int hi = (int)floor(b.o[k] + e) + 2;
         if (!(d.periodic & (1u << k))) {
@@ -969,15 +996,15 @@ __device__ __noinline__ Bounce<typename Sto<S>::R> bounce_back(const Dev &d, int
     const int qb = opp(q);
     const R own = Sto<S>::ld(d.fsrc, qb, i, d.N);
     if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
-    if (ns != CL_O) return Bounce<R>{own, R(0)};
+    if (ns != CL_O && !(ns == CL_WALL && d.walls_move)) return Bounce<R>{own, R(0)};
     if constexpr (S == 0) {
-        const double cuw = link_cuw(d, d.bodies[d.bid[si]], x, y, z, q);
+        const double cuw = ns == CL_O ? link_cuw(d, d.bodies[d.bid[si]], x, y, z, q) : wall_cuw(d, x, y, z, q);
         if (cuw == 0.0) return Bounce<R>{own, 0.0};
         const double rho_x = cell_density<S>(d, d.fsrc, i);
         const double src = ((6.0 * wd(q)) * rho_x) * cuw;
         return Bounce<R>{own + src, src};
     } else {
-        const float cuw = link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q);
+        const float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q) : (float)wall_cuw(d, x, y, z, q);
         if (cuw == 0.0f) return Bounce<R>{own, 0.0f};
         float dr = 0.0f;
 #pragma unroll
@@ -1119,7 +1146,7 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
 #pragma unroll
             for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
             fp[0] = P::ld(d.fsrc, 0, i, N);
-        } else if (c == CL_L && !d.periodic) {
+        } else if (c == CL_L && !d.periodic && !d.walls_move) {
             // on a face of a grid without periodic axes, no obstacle
             // neighbour: a source beyond a face is a resting wall, which
             // returns the cell's own opposite population (Eq. noslip, u_w = 0)
@@ -1132,7 +1159,7 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
                 fp[q] = out ? P::ld(d.fsrc, opp(q), i, N) : P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
             }
             fp[0] = P::ld(d.fsrc, 0, i, N);
-        } else if (c == CL_L) {
+        } else if (c == CL_L && !d.walls_move) {
             // on a face with periodic axes: pull across the seams, walls as above
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -1534,7 +1561,8 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             for (int q = 1; q < Q; ++q) {
                 int qb = opp(q);
                 if (scl[q] == CL_WALL || scl[q] == CL_O) {
-                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q) : 0.0;
+                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q)
+                                                : (d.walls_move ? wall_cuw(d, x, y, z, q) : 0.0);
                     fp[q] = fo[qb] + ((6.0 * wd(q)) * rho_x) * cuw;
                 } else if (scl[q] == CL_G) {
                     fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
@@ -1618,7 +1646,8 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                 int ns = cls(d, si);
                 if (ns == CL_WALL || ns == CL_O) {
                     solid |= 1u << q;
-                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q) : 0.0f;
+                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
+                                           : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
                     fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
                 } else if (ns == CL_G) {
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
@@ -1929,10 +1958,18 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
         b.Tp[k] = b.T[k];
     }
     b.nF = 1;
-    double vol = ((8.0 * b.h[0]) * b.h[1]) * b.h[2];
-    double mass = b.dens * vol;
-    double I[3] = {(mass / 3.0) * (b.h[1] * b.h[1] + b.h[2] * b.h[2]), (mass / 3.0) * (b.h[0] * b.h[0] + b.h[2] * b.h[2]),
-                   (mass / 3.0) * (b.h[0] * b.h[0] + b.h[1] * b.h[1])};
+    double vol, mass, I[3];
+    if (b.shape == 1) {  // sphere: V = 4/3 pi r^3, I = 2/5 m r^2
+        vol = 4.1887902047863905 * ((b.h[0] * b.h[0]) * b.h[0]);
+        mass = b.dens * vol;
+        I[0] = I[1] = I[2] = (0.4 * mass) * (b.h[0] * b.h[0]);
+    } else {
+        vol = ((8.0 * b.h[0]) * b.h[1]) * b.h[2];
+        mass = b.dens * vol;
+        I[0] = (mass / 3.0) * (b.h[1] * b.h[1] + b.h[2] * b.h[2]);
+        I[1] = (mass / 3.0) * (b.h[0] * b.h[0] + b.h[2] * b.h[2]);
+        I[2] = (mass / 3.0) * (b.h[0] * b.h[0] + b.h[1] * b.h[1]);
+    }
     double If[3] = {I[0] / b.dens, I[1] / b.dens, I[2] / b.dens};
     double den = mass + VIRTUAL_MASS * vol;
     for (int k = 0; k < 3; ++k) {
@@ -1993,7 +2030,9 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     // (the paper's rigid-body engine); report it instead of running on
     for (int k = 0; k < 3; ++k) {
         if (d.periodic & (1u << k)) continue;
-        const double e = (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) + fabs(b.R[k * 3 + 2]) * b.h[2];
+        const double e = b.shape == 1 ? b.h[0]
+                                      : (fabs(b.R[k * 3 + 0]) * b.h[0] + fabs(b.R[k * 3 + 1]) * b.h[1]) +
+                                            fabs(b.R[k * 3 + 2]) * b.h[2];
         const double n = k == 0 ? d.nx : (k == 1 ? d.ny : d.nz);
         if (b.o[k] - e < 0.0 || b.o[k] + e > n) atomicOr(d.status, ST_CONTACT);
     }

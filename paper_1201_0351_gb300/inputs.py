@@ -416,3 +416,24 @@ def floating_cubes(steps: int = 40000) -> Scenario:
                          density_ratio=dens, mode=MODE_ROT_AXIS_ONLY, rot_axis=(1.0, 0.0, 0.0)))
     return Scenario("floating_cubes_130x40x40", nx, ny, nz, 0, 1.0 / 1.9, (0.0, 0.0, -g), (0.0, 0.0, 0.0), 1.0, 1e-2,
                     flags, fill, rho, boxes, steps)
+
+
+def free_advection_channel(tau: float = 0.8, u: float = 1e-4, g: float = 1e-5, steps: int = 20000,
+                           nx: int = 60, ny: int = 40, nz: int = 30, radius: float = 6.0,
+                           depth: float = 19.5) -> Scenario:
+    """The free-advection test of Sec. 3.2.1: a 60x40x30 channel, periodic in
+    x, filled to `depth` (19.5), whose bottom and long side walls move with
+    (u, 0, 0) (the top, in the gas, rests); the liquid starts uniform at u; a
+    sphere of diameter 12 and density 0.5 floats half immersed at the centre,
+    starting at rest, and should end up moving with the liquid."""
+    flags, fill, rho = hydrostatic_tank(nx, ny, nz, lambda X, Y: depth, g, 1.0, 1)
+    vel = np.zeros((nx * ny * nz, 3))
+    vel[(flags == LIQUID) | (flags == INTERFACE), 0] = u
+    wall = [0.0] * 18
+    for face in (2, 3, 4):  # y-, y+, z-
+        wall[3 * face] = u
+    sphere = Box(center=(nx / 2.0, ny / 2.0, depth), half=(radius, radius, radius), density_ratio=0.5,
+                 mode=MODE_FREE, shape=SHAPE_SPHERE)
+    return Scenario("free_advection_%dx%dx%d_tau%g_u%g" % (nx, ny, nz, tau, u), nx, ny, nz, 1, tau, (0.0, 0.0, -g),
+                    (0.0, 0.0, 0.0), 1.0, 1e-2, flags, fill, rho, [sphere], steps, vel=vel.reshape(-1),
+                    wall_vel=tuple(wall))

@@ -34,13 +34,15 @@ class lbm_fs_params(C.Structure):
                 ("init_flags", C.c_void_p), ("init_fill", C.c_void_p), ("init_rho", C.c_void_p),
                 ("init_vel", C.c_void_p), ("init_on_device", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("use_graphs", C.c_int32), ("sigma", C.c_double)]
+                ("stream", C.c_void_p), ("use_graphs", C.c_int32), ("sigma", C.c_double),
+                ("wall_vel", C.c_double * 18)]
 
 
 class lbm_fs_box(C.Structure):
     _fields_ = [("center", C.c_double * 3), ("half", C.c_double * 3), ("quat", C.c_double * 4),
                 ("density_ratio", C.c_double), ("vel", C.c_double * 3), ("omega", C.c_double * 3),
-                ("mode", C.c_int32), ("rot_axis", C.c_double * 3), ("lin_damping", C.c_double)]
+                ("mode", C.c_int32), ("rot_axis", C.c_double * 3), ("lin_damping", C.c_double),
+                ("shape", C.c_int32)]
 
 
 class lbm_fs_body_state_t(C.Structure):
@@ -307,6 +309,7 @@ def make_box(b) -> lbm_fs_box:
     box.mode = int(b.mode)
     box.rot_axis[:] = [float(v) for v in b.rot_axis]
     box.lin_damping = float(b.lin_damping)
+    box.shape = int(getattr(b, "shape", 0))
     return box
 
 
@@ -346,6 +349,9 @@ def scenario_params(sc, storage: str, stream: int, use_graphs: bool, alloc=None,
     p.stream = stream
     p.use_graphs = 1 if use_graphs else 0
     p.sigma = float(getattr(sc, "sigma", 0.0) or 0.0)
+    wall_vel = getattr(sc, "wall_vel", None)
+    if wall_vel is not None:
+        p.wall_vel[:] = [float(v) for v in np.asarray(wall_vel, dtype=np.float64).reshape(18)]
     return p
 
 
