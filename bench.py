@@ -129,6 +129,21 @@ def fluid_counts(sim):
     return int(((fl == 1) | (fl == 2)).sum()), int((fl == 1).sum()), int((fl == 2).sum())
 
 
+def whole_job(ms_local: float, cells: int, steps: int, world: int, device: str = "cpu"):
+    """Replicas (one tank per rank, no data-path collective): the job's time is
+    the slowest rank's, and the job's throughput counts every rank's cells.
+    Returns (max milliseconds over ranks, whole-job MLUPS)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * cells * steps / (ms * 1e-3) / 1e6
+
+
 def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=None):
     import torch
 
@@ -385,13 +400,8 @@ def main():
 
         batch = run_batch(inputs.batched_sweep_tanks(64), "f16s", args.steps, max(args.warmup, 3), 5,
                           barrier=barrier)
-    ms = main_run["ms_total"]
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     n = sc.nx * sc.ny * sc.nz
-    value = ws * n * args.steps / (ms * 1e-3) / 1e6
+    ms, value = whole_job(main_run["ms_total"], n, args.steps, ws, "cuda")
     e2e = e2e_run(sc, "f32", args.e2e_steps or sc.steps)
     e2e["value"] *= ws
     if rank != 0:
