@@ -574,11 +574,26 @@ static void conversions(orc_sim *s) {
     long n = s->n;
     uint8_t *mark = (uint8_t *)calloc(n, 1);
     for (int k = 0; k < 6; ++k) s->counts[k] = 0;
-    /* (1) marks */
+    /* (1) marks: the fill-level thresholds; and (R23) an interface cell
+     * without a liquid neighbour empties, one without a gas neighbour fills
+     * (the classes at t; walls and obstacles count as neither) */
     for (long i = 0; i < n; ++i) {
         if (s->flag[i] != IFC) continue;
-        if (s->phin[i] >= 1.0 + s->eps) mark[i] |= CV_FILLED;
-        else if (s->phin[i] <= -s->eps) mark[i] |= CV_EMPTIED;
+        if (s->phin[i] >= 1.0 + s->eps) {
+            mark[i] |= CV_FILLED;
+        } else if (s->phin[i] <= -s->eps) {
+            mark[i] |= CV_EMPTIED;
+        } else if (g_mutation != 9) {
+            int x = (int)(i % s->nx), y = (int)((i / s->nx) % s->ny), z = (int)(i / ((long)s->nx * s->ny));
+            int liq = 0, gas = 0;
+            for (int q = 1; q < Q; ++q) {
+                int c = class_of(s, neighbour(s, x, y, z, C[q][0], C[q][1], C[q][2]));
+                liq |= c == LIQ;
+                gas |= c == GAS;
+            }
+            if (!liq && gas) mark[i] |= CV_EMPTIED;
+            else if (!gas && liq) mark[i] |= CV_FILLED;
+        }
     }
     /* (2) filled cells: gas neighbours become interface; emptied neighbours are kept */
     for (int z = 0; z < s->nz; ++z)

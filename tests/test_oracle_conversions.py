@@ -156,3 +156,74 @@ def test_box_moving_through_surface_uncovers_liquid_interface_gas():
     fl = s.fields()["fill"].reshape(n, n, n)
     assert np.all(np.abs(fl[6, 4:8, 2] - 0.5) < 0.05)
     assert _ledger_ok(s)
+
+
+def _pool_with_cell(cell_class, fill_value):
+    """A 12^3 closed tank, liquid below z = 4 and an interface layer at z = 4,
+    plus one extra cell at (6, 6, 9) of the given class and fill level."""
+    n = 12
+    flags = np.full((n, n, n), I.GAS, np.uint8)
+    fill = np.zeros((n, n, n))
+    flags[:4] = I.LIQUID
+    fill[:4] = 1.0
+    flags[4] = I.INTERFACE
+    fill[4] = 0.5
+    flags[9, 6, 6] = cell_class
+    fill[9, 6, 6] = fill_value
+    if cell_class == I.INTERFACE and fill_value > 0.9:
+        # an interface cell enclosed by liquid: a liquid blob around it
+        flags[8:11, 5:8, 5:8] = I.LIQUID
+        fill[8:11, 5:8, 5:8] = 1.0
+        flags[9, 6, 6] = I.INTERFACE
+        fill[9, 6, 6] = fill_value
+        shell = np.zeros_like(flags, dtype=bool)
+        shell[7:12, 4:9, 4:9] = True
+        shell[8:11, 5:8, 5:8] = False
+        flags[shell] = I.INTERFACE
+        fill[shell] = 0.5
+    return I.Scenario("pool_cell", n, n, n, 0, 0.8, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0, 1e-2,
+                      flags.reshape(-1), fill.reshape(-1), np.ones(n ** 3), [], 10)
+
+
+def _ledger_closes(ref):
+    lg = ref.ledger()
+    assert abs(lg["M"] - lg["M0"] - (lg["uncovered"] - lg["covered"] - lg["lost"] + lg["wall"])) <= 1e-12 * lg["M0"]
+
+
+def test_interface_cell_without_liquid_neighbour_empties():
+    """A lone interface cell in the gas (a splash with fill 0.3, no liquid
+    neighbour) becomes gas at the next step; with no interface neighbour its
+    mass leaves through the lost-excess ledger, and the ledger closes."""
+    sc = _pool_with_cell(I.INTERFACE, 0.3)
+    i = 6 + 12 * (6 + 12 * 9)
+    ref = oracle.OracleSim(sc)
+    m0 = ref.fields()["mass"][i]
+    ref.step(1)
+    f = ref.fields()
+    assert f["flags"][i] == I.GAS and f["mass"][i] == 0.0
+    assert abs(ref.ledger()["lost"] - m0) <= 1e-14
+    _ledger_closes(ref)
+    assert ref.error == 0
+
+
+def test_interface_cell_without_gas_neighbour_fills():
+    """An interface cell enclosed by liquid (fill 0.95, no gas neighbour)
+    becomes liquid at the next step."""
+    sc = _pool_with_cell(I.INTERFACE, 0.95)
+    i = 6 + 12 * (6 + 12 * 9)
+    ref = oracle.OracleSim(sc)
+    ref.step(1)
+    assert ref.fields()["flags"][i] == I.LIQUID
+    _ledger_closes(ref)
+    assert ref.error == 0
+
+
+def test_neighbour_rule_mutation_is_caught():
+    oracle.set_mutation(9)
+    try:
+        ref = oracle.OracleSim(_pool_with_cell(I.INTERFACE, 0.3))
+        ref.step(1)
+        flag = ref.fields()["flags"][6 + 12 * (6 + 12 * 9)]
+    finally:
+        oracle.set_mutation(0)
+    assert flag == I.INTERFACE
