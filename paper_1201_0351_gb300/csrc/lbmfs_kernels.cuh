@@ -771,160 +771,158 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
     const float of[3] = {(float)b.o[0], (float)b.o[1], (float)b.o[2]};
     const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
     const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
-    // z-planes over blocks, (x, y) over the block's 32 x 8 threads; only cells
-    // next to an obstacle (neighbour-obstacle bit) can hold links
-    for (int zz = lo[2] + (int)vb.x; zz < hi[2]; zz += vb.nx) {
-        int z = zz < 0 ? zz + d.nz : (zz >= d.nz ? zz - d.nz : zz);
-        for (int yy = lo[1] + (int)threadIdx.y; yy < hi[1]; yy += blockDim.y) {
-            int y = yy < 0 ? yy + d.ny : (yy >= d.ny ? yy - d.ny : yy);
-            for (int xx = lo[0] + (int)threadIdx.x; xx < hi[0]; xx += blockDim.x) {
-                int x = xx < 0 ? xx + d.nx : (xx >= d.nx ? xx - d.nx : xx);
-                long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
-                int fb = d.flags[i];
-                int cl = fb & CL_MASK;
-                if (!(fb & NB_OBST) || cl == CL_O) continue;
-                if constexpr (S == 0) {
-                    // double, in the order of the plain restatement
-                    const double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
-                    const double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
-                                         min_image(d, (z + 0.5) - b.o[2], 2)};
-                    bool have_rho = false;
-                    double rho_x = 0.0;
+    // the cells of the box around the body spread over all the body's blocks
+    // (a fixed cell-to-thread map: the sums below stay deterministic); only
+    // cells next to an obstacle (neighbour-obstacle bit) can hold links
+    const long long ncell = range_count(lo, hi);
+    const int tidf = threadIdx.x + blockDim.x * threadIdx.y, nthr = blockDim.x * blockDim.y;
+    for (long long kk = (long long)vb.x * nthr + tidf; kk < ncell; kk += (long long)vb.nx * nthr) {
+        int x, y, z;
+        range_cell(d, lo, hi, kk, x, y, z);
+        long long i = x + (long long)d.nx * (y + (long long)d.ny * z);
+        int fb = d.flags[i];
+        int cl = fb & CL_MASK;
+        if (!(fb & NB_OBST) || cl == CL_O) continue;
+        if constexpr (S == 0) {
+            // double, in the order of the plain restatement
+            const double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
+            const double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
+                                 min_image(d, (z + 0.5) - b.o[2], 2)};
+            bool have_rho = false;
+            double rho_x = 0.0;
 #pragma unroll 1
-                    for (int q = 1; q < Q; ++q) {
-                        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                        if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
-                        double cuw = link_cuw(d, b, x, y, z, q);
-                        int qb = opp(q);
-                        double inner;
-                        if (cl == CL_G) {
-                            inner = wd(q) * d.rho_g;
-                        } else {
-                            double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
-                            double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
-                            double C;
-                            if (cuw == 0.0) {
-                                C = phi_x * 0.0;
-                            } else {
-                                if (!have_rho) {
-                                    rho_x = cell_density<S>(d, d.fsrc, i);
-                                    have_rho = true;
-                                }
-                                C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
-                            }
-                            inner = (A + B) + C;
-                        }
-                        double g = 2.0 * inner;
-                        double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
-                        acc[0] += F0;
-                        acc[1] += F1;
-                        acc[2] += F2;
-                        acc[3] += r[1] * F2 - r[2] * F1;
-                        acc[4] += r[2] * F0 - r[0] * F2;
-                        acc[5] += r[0] * F1 - r[1] * F0;
-                        acc[6] += fabs(g);
-                    }
+            for (int q = 1; q < Q; ++q) {
+                long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                if (si < 0 || clsv(d, si) != CL_O || d.bid[si] != bi) continue;
+                double cuw = link_cuw(d, b, x, y, z, q);
+                int qb = opp(q);
+                double inner;
+                if (cl == CL_G) {
+                    inner = wd(q) * d.rho_g;
                 } else {
-                    // reduced-precision storage: the link term is split into the
-                    // uniform gas-pressure part 2 w_q rho_G (double) and the small
-                    // remainder 2 (phi (f_qbar - w_q rho_G) + moving-wall part),
-                    // computed in float from the stored deviations f - w.  The
-                    // lever arm r is the cell's, so each part is summed over the
-                    // cell's links first and its torque is r x that sum.
-                    // Directions into body bi: all neighbour classes requested
-                    // at once, then the body ids of the obstacle directions.
-                    unsigned om = 0, lm = 0;
-#pragma unroll
-                    for (int q = 1; q < Q; ++q) {
-                        const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                        if (si >= 0 && clsv(d, si) == CL_O) om |= 1u << q;
+                    double A = phi_x * Sto<S>::ldf(d.fsrc, qb, i, d.N);
+                    double B = (1.0 - phi_x) * (wd(q) * d.rho_g);
+                    double C;
+                    if (cuw == 0.0) {
+                        C = phi_x * 0.0;
+                    } else {
+                        if (!have_rho) {
+                            rho_x = cell_density<S>(d, d.fsrc, i);
+                            have_rho = true;
+                        }
+                        C = phi_x * (((3.0 * wd(q)) * rho_x) * cuw);
                     }
-#pragma unroll
-                    for (int q = 1; q < Q; ++q)
-                        if (om & (1u << q))
-                            if (d.bid[nbr(d, x, y, z, -cx(q), -cy(q), -cz(q))] == bi) lm |= 1u << q;
-                    if (!lm) continue;
-                    const float phf = cl == CL_L ? 1.0f : (cl == CL_I ? (float)d.phisrc[i] : 0.0f);
-                    const float rg = (float)d.rho_g, wrg1 = d.rg1_f;
-                    // lever arm from the cell centre (minimum image on periodic
-                    // axes): float for the small remainder, and twice the cell
-                    // centre as an integer for the exact gas-pressure part
-                    const int xyz[3] = {x, y, z}, nn[3] = {d.nx, d.ny, d.nz};
-                    float rf[3];
-                    long long c2[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        int xk = xyz[k];
-                        rf[k] = ((float)xk + 0.5f) - of[k];
-                        if (d.periodic & (1u << k)) {
-                            const int sh = (int)floorf(rf[k] / (float)nn[k] + 0.5f);
-                            xk -= sh * nn[k];
-                            rf[k] -= (float)(sh * nn[k]);
-                        }
-                        c2[k] = 2ll * xk + 1;
-                    }
-                    float rho_x = -1.0f;
-                    int kx = 0, ky = 0, kz = 0;  // sum of 36 (2 w_q) c_qbar over the links
-                    float gx = 0.0f, gy = 0.0f, gz = 0.0f, fabs_sum = 0.0f;
-#pragma unroll
-                    for (int q = 1; q < Q; ++q) {
-                        if (!(lm & (1u << q))) continue;
-                        const int qb = opp(q);
-                        const int m36 = q <= 6 ? 4 : 2;  // 36 x 2 w_q
-                        float gdev = 0.0f;
-                        if (cl != CL_G) {
-                            // u_w at the link midpoint, r + c_qbar / 2 from the body centre
-                            const float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb),
-                                        pz = rf[2] + 0.5f * cz(qb);
-                            const float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
-                            const float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
-                            const float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
-                            const float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-                            float C = 0.0f;
-                            if (cuw != 0.0f) {
-                                if (rho_x < 0.0f) {
-                                    float dr = 0.0f;
-#pragma unroll
-                                    for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
-                                    rho_x = 1.0f + dr;
-                                }
-                                C = phf * (3.0f * wf(q) * rho_x * cuw);
-                            }
-                            const float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
-                            gdev = 2.0f * (phf * dev + C);
-                        }
-                        if (cx(qb)) {
-                            kx += cx(qb) * m36;
-                            gx += cx(qb) * gdev;
-                        }
-                        if (cy(qb)) {
-                            ky += cy(qb) * m36;
-                            gy += cy(qb) * gdev;
-                        }
-                        if (cz(qb)) {
-                            kz += cz(qb) * m36;
-                            gz += cz(qb) * gdev;
-                        }
-                        fabs_sum += fabsf((float)m36 * (rg * (1.0f / 36.0f)) + gdev);
-                    }
-                    // remainder: the cell's links in float, cells in double
-                    acc[0] += (double)gx;
-                    acc[1] += (double)gy;
-                    acc[2] += (double)gz;
-                    acc[3] += (double)(rf[1] * gz - rf[2] * gy);
-                    acc[4] += (double)(rf[2] * gx - rf[0] * gz);
-                    acc[5] += (double)(rf[0] * gy - rf[1] * gx);
-                    acc[6] += (double)fabs_sum;
-                    // gas-pressure part (rho_G / 36) K, exactly in integers:
-                    // its torque is (rho_G / 36) (sum c2 x K / 2 - o x sum K)
-                    ik[0] += kx;
-                    ik[1] += ky;
-                    ik[2] += kz;
-                    it[0] += c2[1] * kz - c2[2] * ky;
-                    it[1] += c2[2] * kx - c2[0] * kz;
-                    it[2] += c2[0] * ky - c2[1] * kx;
+                    inner = (A + B) + C;
                 }
+                double g = 2.0 * inner;
+                double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
+                acc[0] += F0;
+                acc[1] += F1;
+                acc[2] += F2;
+                acc[3] += r[1] * F2 - r[2] * F1;
+                acc[4] += r[2] * F0 - r[0] * F2;
+                acc[5] += r[0] * F1 - r[1] * F0;
+                acc[6] += fabs(g);
             }
+        } else {
+            // reduced-precision storage: the link term is split into the
+            // uniform gas-pressure part 2 w_q rho_G (double) and the small
+            // remainder 2 (phi (f_qbar - w_q rho_G) + moving-wall part),
+            // computed in float from the stored deviations f - w.  The
+            // lever arm r is the cell's, so each part is summed over the
+            // cell's links first and its torque is r x that sum.
+            // Directions into body bi: all neighbour classes requested
+            // at once, then the body ids of the obstacle directions.
+            unsigned om = 0, lm = 0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                if (si >= 0 && clsv(d, si) == CL_O) om |= 1u << q;
+            }
+#pragma unroll
+            for (int q = 1; q < Q; ++q)
+                if (om & (1u << q))
+                    if (d.bid[nbr(d, x, y, z, -cx(q), -cy(q), -cz(q))] == bi) lm |= 1u << q;
+            if (!lm) continue;
+            const float phf = cl == CL_L ? 1.0f : (cl == CL_I ? (float)d.phisrc[i] : 0.0f);
+            const float rg = (float)d.rho_g, wrg1 = d.rg1_f;
+            // lever arm from the cell centre (minimum image on periodic
+            // axes): float for the small remainder, and twice the cell
+            // centre as an integer for the exact gas-pressure part
+            const int xyz[3] = {x, y, z}, nn[3] = {d.nx, d.ny, d.nz};
+            float rf[3];
+            long long c2[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                int xk = xyz[k];
+                rf[k] = ((float)xk + 0.5f) - of[k];
+                if (d.periodic & (1u << k)) {
+                    const int sh = (int)floorf(rf[k] / (float)nn[k] + 0.5f);
+                    xk -= sh * nn[k];
+                    rf[k] -= (float)(sh * nn[k]);
+                }
+                c2[k] = 2ll * xk + 1;
+            }
+            float rho_x = -1.0f;
+            int kx = 0, ky = 0, kz = 0;  // sum of 36 (2 w_q) c_qbar over the links
+            float gx = 0.0f, gy = 0.0f, gz = 0.0f, fabs_sum = 0.0f;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                if (!(lm & (1u << q))) continue;
+                const int qb = opp(q);
+                const int m36 = q <= 6 ? 4 : 2;  // 36 x 2 w_q
+                float gdev = 0.0f;
+                if (cl != CL_G) {
+                    // u_w at the link midpoint, r + c_qbar / 2 from the body centre
+                    const float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb),
+                                pz = rf[2] + 0.5f * cz(qb);
+                    const float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
+                    const float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
+                    const float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
+                    const float cuw = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+                    float C = 0.0f;
+                    if (cuw != 0.0f) {
+                        if (rho_x < 0.0f) {
+                            float dr = 0.0f;
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
+                            rho_x = 1.0f + dr;
+                        }
+                        C = phf * (3.0f * wf(q) * rho_x * cuw);
+                    }
+                    const float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
+                    gdev = 2.0f * (phf * dev + C);
+                }
+                if (cx(qb)) {
+                    kx += cx(qb) * m36;
+                    gx += cx(qb) * gdev;
+                }
+                if (cy(qb)) {
+                    ky += cy(qb) * m36;
+                    gy += cy(qb) * gdev;
+                }
+                if (cz(qb)) {
+                    kz += cz(qb) * m36;
+                    gz += cz(qb) * gdev;
+                }
+                fabs_sum += fabsf((float)m36 * (rg * (1.0f / 36.0f)) + gdev);
+            }
+            // remainder: the cell's links in float, cells in double
+            acc[0] += (double)gx;
+            acc[1] += (double)gy;
+            acc[2] += (double)gz;
+            acc[3] += (double)(rf[1] * gz - rf[2] * gy);
+            acc[4] += (double)(rf[2] * gx - rf[0] * gz);
+            acc[5] += (double)(rf[0] * gy - rf[1] * gx);
+            acc[6] += (double)fabs_sum;
+            // gas-pressure part (rho_G / 36) K, exactly in integers:
+            // its torque is (rho_G / 36) (sum c2 x K / 2 - o x sum K)
+            ik[0] += kx;
+            ik[1] += ky;
+            ik[2] += kz;
+            it[0] += c2[1] * kz - c2[2] * ky;
+            it[1] += c2[2] * kx - c2[0] * kz;
+            it[2] += c2[0] * ky - c2[1] * kx;
         }
     }
     // deterministic block reduction (fixed shuffle tree, then warps in order);
@@ -1517,10 +1515,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
         if constexpr (!P::shifted) {
             long long src[Q];
             int scl[Q];
+            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
                 scl[q] = cls(d, src[q]);
+                has_l = has_l || scl[q] == CL_L;
+                has_g = has_g || scl[q] == CL_G;
             }
             // normal n = -grad(phi), central differences
             double nv[3];
@@ -1605,6 +1606,9 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             d.phidst[i] = phin;
             if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
             uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+            // an interface cell without a liquid neighbour empties, one without
+            // a gas neighbour fills
+            if (!mk) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
             if (mk) d.cmark[i] = mk;
             wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
@@ -1639,11 +1643,14 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             }
             fp[0] = fo[0];
             unsigned solid = 0;  // directions whose source is an obstacle or a wall
+            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 int qb = opp(q);
                 long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
                 int ns = cls(d, si);
+                has_l = has_l || ns == CL_L;
+                has_g = has_g || ns == CL_G;
                 if (ns == CL_WALL || ns == CL_O) {
                     solid |= 1u << q;
                     float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
@@ -1692,6 +1699,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             d.phidst[i] = phin;
             if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
             uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+            if (!mk) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
             if (mk) d.cmark[i] = mk;
             wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
@@ -1919,9 +1927,9 @@ __global__ void k_conv_finish(const __grid_constant__ Dev d) { conv_finish_body<
 // ----------------------------------------------- C5: rigid-body update
 
 // one warp per body: fixed-order sum of the force partials, then the update
+__device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *acc);
 __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     int bi = vb.x;
-    Body &b = d.bodies[bi];
     int lane = threadIdx.x;
     double acc[7];
 #pragma unroll
@@ -1932,6 +1940,14 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
         acc[c] = v;
     }
     if (lane != 0) return;
+    // the body record is read once into registers, updated, and written back
+    // (instead of a chain of dependent global-memory reads and writes)
+    Body b = d.bodies[bi];
+    body_step(d, b, acc);
+    d.bodies[bi] = b;
+}
+
+__device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *acc) {
     for (int k = 0; k < 3; ++k) {
         b.F[k] = acc[k];
         b.T[k] = acc[3 + k];

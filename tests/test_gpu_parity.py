@@ -203,3 +203,13 @@ def test_box_reaching_a_wall_is_reported():
         sim.sync()
     sim.close()
     assert e.value.code == lbm_fs.LBM_FS_EUNSTABLE and "wall" in str(e.value)
+
+
+@pytest.mark.parametrize("fill_value", [0.3, 0.95])
+def test_neighbour_conversion_rule_parity(fill_value):
+    """A lone splash cell (no liquid neighbour) and an enclosed interface cell
+    (no gas neighbour) convert as in the oracle."""
+    import test_oracle_conversions as T
+
+    g, o, gb, ob, gs, ref = run_both(T._pool_with_cell(I.INTERFACE, fill_value), 20, storage="f64")
+    assert_f64_parity(g, o, gb, ob)
