@@ -88,6 +88,9 @@ constexpr int CL_WALL = 256;
 // ----------------------------------------------------------------- storage
 // population loads / stores (tuning knob: evict-first stores)
 template <class T> __device__ __forceinline__ T pop_ld(const T *p) { return *p; }
+// through the read-only data path: only for a grid that no thread of the
+// launch writes (the bulk kernel's source populations)
+template <class T> __device__ __forceinline__ T pop_ldg(const T *p) { return __ldg(p); }
 template <class T> __device__ __forceinline__ void pop_st(T *p, T v) {
 #if LBMFS_ST_CS
     __stcs(p, v);
@@ -102,6 +105,9 @@ template <> struct Sto<0> {
     static constexpr bool shifted = false;
     static __device__ __forceinline__ double ld(const void *g, int q, long long i, long long N) {
         return pop_ld(reinterpret_cast<const double *>(g) + ((long long)q * N + i));
+    }
+    static __device__ __forceinline__ double ldg(const void *g, int q, long long i, long long N) {
+        return pop_ldg(reinterpret_cast<const double *>(g) + ((long long)q * N + i));
     }
     static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, double v) {
         pop_st(reinterpret_cast<double *>(g) + ((long long)q * N + i), v);
@@ -123,6 +129,9 @@ template <> struct Sto<1> {
     static constexpr bool shifted = true;
     static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
         return pop_ld(reinterpret_cast<const float *>(g) + ((long long)q * N + i));
+    }
+    static __device__ __forceinline__ float ldg(const void *g, int q, long long i, long long N) {
+        return pop_ldg(reinterpret_cast<const float *>(g) + ((long long)q * N + i));
     }
     static __device__ __forceinline__ void st(void *g, int q, long long i, long long N, float v) {
         pop_st(reinterpret_cast<float *>(g) + ((long long)q * N + i), v);
@@ -165,6 +174,10 @@ template <> struct Sto<2> {
     static __device__ __forceinline__ float ld(const void *g, int q, long long i, long long N) {
         if (q == 0) return pop_ld(reinterpret_cast<const float *>(g) + i);
         return __half2float(pop_ld(hp(g, N) + ((long long)(q - 1) * N + i))) * F16_INV_SCALE;
+    }
+    static __device__ __forceinline__ float ldg(const void *g, int q, long long i, long long N) {
+        if (q == 0) return pop_ldg(reinterpret_cast<const float *>(g) + i);
+        return __half2float(pop_ldg(hp(g, N) + ((long long)(q - 1) * N + i))) * F16_INV_SCALE;
     }
     static __device__ __forceinline__ double ldf(const void *g, int q, long long i, long long N) {
         return wd(q) + (double)ld(g, q, i, N);
@@ -1142,8 +1155,8 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
             // no obstacle or wall in the neighbourhood and a liquid cell never
             // touches gas: plain pull from the 18 neighbours
 #pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
-            fp[0] = P::ld(d.fsrc, 0, i, N);
+            for (int q = 1; q < Q; ++q) fp[q] = P::ldg(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            fp[0] = P::ldg(d.fsrc, 0, i, N);
         } else if (c == CL_L && !d.periodic && !d.walls_move) {
             // on a face of a grid without periodic axes, no obstacle
             // neighbour: a source beyond a face is a resting wall, which
@@ -1154,17 +1167,17 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
             for (int q = 1; q < Q; ++q) {
                 const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
                                  (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
-                fp[q] = out ? P::ld(d.fsrc, opp(q), i, N) : P::ld(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+                fp[q] = out ? P::ldg(d.fsrc, opp(q), i, N) : P::ldg(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
             }
-            fp[0] = P::ld(d.fsrc, 0, i, N);
+            fp[0] = P::ldg(d.fsrc, 0, i, N);
         } else if (c == CL_L && !d.walls_move) {
             // on a face with periodic axes: pull across the seams, walls as above
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                fp[q] = si >= 0 ? P::ld(d.fsrc, q, si, N) : P::ld(d.fsrc, opp(q), i, N);
+                fp[q] = si >= 0 ? P::ldg(d.fsrc, q, si, N) : P::ldg(d.fsrc, opp(q), i, N);
             }
-            fp[0] = P::ld(d.fsrc, 0, i, N);
+            fp[0] = P::ldg(d.fsrc, 0, i, N);
         } else {
             gather_general<S>(d, x, y, z, i, fp);
         }
