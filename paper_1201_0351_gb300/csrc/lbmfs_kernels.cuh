@@ -1627,12 +1627,6 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
         } else {
             float phx = (float)own_phi;
-            float nv0 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi) -
-                                (float)fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi));
-            float nv1 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi) -
-                                (float)fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi));
-            float nv2 = 0.5f * ((float)fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi) -
-                                (float)fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi));
             float fo[Q], fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
@@ -1646,6 +1640,52 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             }
             float rx = 1.0f + drx;
             float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
+            // One walk over the 18 neighbours s = x - c_q: the class decides the
+            // arriving population (pull, or Eq. noslip from an obstacle or a
+            // wall; gas sources are reconstructed below); a liquid or interface
+            // source also gives the Sec. 2.2 mass exchange of the link back to
+            // it, f_q(s) - f_qbar(x) (weighted by the mean fill for interface
+            // neighbours), and the axis neighbours give the fill levels of the
+            // normal (1 / phi / 0 for liquid / interface / gas, own phi else).
+            fp[0] = fo[0];
+            unsigned solid = 0, gas = 0;  // directions whose source is solid / gas
+            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
+            float dm = 0.0f;
+            float fs[7];  // fill level seen at the source of each axis direction
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const int qb = opp(q);
+                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                const int ns = cls(d, si);
+                has_l = has_l || ns == CL_L;
+                has_g = has_g || ns == CL_G;
+                float seen = phx;
+                if (ns == CL_WALL || ns == CL_O) {
+                    solid |= 1u << q;
+                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
+                                           : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
+                    fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
+                } else if (ns == CL_G) {
+                    gas |= 1u << q;
+                    fp[q] = 0.0f;
+                    seen = 0.0f;
+                } else {
+                    const float pq = P::ld(d.fsrc, q, si, N);
+                    fp[q] = pq;
+                    if (ns == CL_L) {
+                        dm += pq - fo[qb];
+                        seen = 1.0f;
+                    } else {
+                        const float phy = (float)d.phisrc[si];
+                        dm += 0.5f * (phx + phy) * (pq - fo[qb]);
+                        seen = phy;
+                    }
+                }
+                if (q <= 6) fs[q] = seen;
+            }
+            // normal n = -grad(phi): W, E, N, S, T, B pull from x + e_x, x - e_x,
+            // x - e_y, x + e_y, x - e_z, x + e_z
+            const float nv0 = 0.5f * (fs[2] - fs[1]), nv1 = 0.5f * (fs[3] - fs[4]), nv2 = 0.5f * (fs[5] - fs[6]);
             float drg = d.drg_f;
             if (d.sigma != 0.0) {
                 // gas density raised by the Laplace pressure
@@ -1654,48 +1694,14 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                             nu2 = len > 0.0f ? nv2 / len : 0.0f;
                 drg = d.drg_f + (6.0f * d.sigma_f) * curvature_f(d, x, y, z, nu0, nu1, nu2);
             }
-            fp[0] = fo[0];
-            unsigned solid = 0;  // directions whose source is an obstacle or a wall
-            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
+            // Eq. reconstruct for gas-sourced directions and every non-solid
+            // direction with c.n below the dead band
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                int qb = opp(q);
-                long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                int ns = cls(d, si);
-                has_l = has_l || ns == CL_L;
-                has_g = has_g || ns == CL_G;
-                if (ns == CL_WALL || ns == CL_O) {
-                    solid |= 1u << q;
-                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
-                                           : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
-                    fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
-                } else if (ns == CL_G) {
+                const float cn = cx(q) * nv0 + cy(q) * nv1 + cz(q) * nv2;
+                if ((gas & (1u << q)) || (cn < -(float)NORMAL_DEADBAND && !(solid & (1u << q)))) {
+                    const int qb = opp(q);
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
-                } else {
-                    fp[q] = P::ld(d.fsrc, q, si, N);
-                }
-            }
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                float cn = cx(q) * nv0 + cy(q) * nv1 + cz(q) * nv2;
-                if (cn < -(float)NORMAL_DEADBAND && !(solid & (1u << q))) {
-                    int qb = opp(q);
-                    fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
-                }
-            }
-            // Sec. 2.2 mass exchange; each link term is computed identically
-            // (up to sign) by both cells, so the exchange stays conservative
-            float dm = 0.0f;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                int qb = opp(q);
-                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                int yc = cls(d, yi);
-                if (yc == CL_L) {
-                    dm += P::ld(d.fsrc, qb, yi, N) - fo[q];
-                } else if (yc == CL_I) {
-                    float wgt = 0.5f * (phx + (float)d.phisrc[yi]);
-                    dm += wgt * (P::ld(d.fsrc, qb, yi, N) - fo[q]);
                 }
             }
             m_new = d.m[i] + (double)dm;
