@@ -180,8 +180,9 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
     n_liq = 0.5 * (n_liq0 + n_liq1)
     n_if = 0.5 * (n_if0 + n_if1)
     b_fluid = BYTES_PER_FLUID[storage]
-    step_bytes = (n_liq + n_if) * b_fluid + n * 1 + n_if * 24
-    liquid_bytes = n_liq * b_fluid + n * 1
+    # one flag byte per fluid cell (tiles of gas above the fluid are never read)
+    step_bytes = (n_liq + n_if) * (b_fluid + 1) + n_if * 24
+    liquid_bytes = n_liq * b_fluid + (n_liq + n_if) * 1
     total_k = sum(kt.values())
     return dict(storage=storage, ms_total=ms, ms_per_step=ms / steps, mlups=n * steps / (ms * 1e-3) / 1e6,
                 fluid_mlups=(n_liq + n_if) * steps / (ms * 1e-3) / 1e6, step_gbs=step_bytes / (ms / steps * 1e-3) / 1e9,
@@ -240,8 +241,8 @@ def run_batch(scenes, storage, steps, warmup, kernel_steps, separate_steps=20, b
     torch.cuda.empty_cache()
     n_liq, n_if = 0.5 * (liq0 + liq1), 0.5 * (if0 + if1)
     b_fluid = BYTES_PER_FLUID[storage]
-    step_bytes = (n_liq + n_if) * b_fluid + cells + n_if * 24
-    liquid_bytes = n_liq * b_fluid + cells
+    step_bytes = (n_liq + n_if) * (b_fluid + 1) + n_if * 24
+    liquid_bytes = n_liq * b_fluid + (n_liq + n_if) * 1
     liquid_ms = kt["liquid"] / kernel_steps
     # the same tanks as separate handles (each with its own captured graphs)
     sims = [lbm_fs.Simulation(sc, storage=storage) for sc in scenes]

@@ -23,7 +23,9 @@
  * Errors: every call returns an lbm_fs_status; nothing is thrown across the
  * ABI.  Invalid arguments give LBM_FS_EINVAL before any allocation.  Device-side
  * conditions (a liquid cell touching gas, a non-finite density, a moving box
- * reaching a domain wall -- contacts are not modelled --, a worklist
+ * reaching a domain wall -- contacts are not modelled --, fluid appearing
+ * more than a few cells above the previous step's fluid top, which the bulk
+ * sweep tracks to skip all-gas tiles and which fluid cannot outrun, a worklist
  * overflow) are sticky bits in a device status word; they are reported as
  * LBM_FS_EUNSTABLE / LBM_FS_EOVERFLOW by the next call that synchronises
  * (lbm_fs_forces, lbm_fs_body_state, lbm_fs_read_fields, lbm_fs_stats,

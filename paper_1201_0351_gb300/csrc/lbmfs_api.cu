@@ -52,6 +52,7 @@ lbm_fs_status read_status(lbm_fs *h) {
     if (st & ST_NONFINITE) return fail(LBM_FS_EUNSTABLE, "non-finite or non-positive density in a fluid cell%s");
     if (st & ST_LIQUID_GAS) return fail(LBM_FS_EUNSTABLE, "a liquid cell touched a gas cell (open interface layer)%s");
     if (st & ST_CONTACT) return fail(LBM_FS_EUNSTABLE, "a moving body reached a domain wall (body-wall contact is not modelled)%s");
+    if (st & ST_TOP) return fail(LBM_FS_EUNSTABLE, "fluid appeared above the bulk kernel's tracked fluid top%s");
     return LBM_FS_OK;
 }
 
@@ -216,9 +217,10 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.red = (double *)h->alloc(sizeof(double) * LIST_BLOCKS);
     double *wallv = (double *)h->alloc(sizeof(double) * 18);
     d.wallv = wallv;
+    int *ztop = (int *)h->alloc(sizeof(int) * 2);
     for (void *ptr : h->allocs)
         if (!ptr) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
-    if (h->allocs.size() != 18 + WL_COUNT) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
+    if (h->allocs.size() != 19 + WL_COUNT) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
     d.walls_move = 0;
     for (int f = 0; f < 6; ++f)
         for (int k = 0; k < 3; ++k)
@@ -240,9 +242,16 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     CKB(cudaMemsetAsync(d.status, 0, 4, st));
     CKB(cudaMemsetAsync(d.part, 0, sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7, st));
     CKB(cudaMemcpyAsync(wallv, &p->wall_vel[0][0], sizeof(double) * 18, cudaMemcpyHostToDevice, st));
+    // the first step visits every tile (its read slot: nz) and records the top
+    const int zt0[2] = {p->nz, -1};
+    CKB(cudaMemcpyAsync(ztop, zt0, sizeof zt0, cudaMemcpyHostToDevice, st));
     h->d[0] = d;
     h->d[1] = d;
     set_grids(h, fA, fB, pA, pB);
+    h->d[0].ztop_rd = ztop;
+    h->d[0].ztop_wr = ztop + 1;
+    h->d[1].ztop_rd = ztop + 1;
+    h->d[1].ztop_wr = ztop;
 
     // upload the initial state (staged through temporary device buffers)
     const uint8_t *dfl = p->init_flags;

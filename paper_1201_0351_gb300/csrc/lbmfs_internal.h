@@ -29,7 +29,10 @@ enum : uint8_t {
     MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_PEND = 32, MK_FRESH = 64
 };
 // sticky device status bits
-enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEOUT = 8, ST_CONTACT = 16 };
+enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEOUT = 8, ST_CONTACT = 16, ST_TOP = 32 };
+// z-planes above the previous step's highest fluid tile that the bulk kernel
+// still visits (fluid rises by at most a cell or two per step)
+constexpr int ZTOP_MARGIN = 4;
 
 // worklists
 enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_COUNT };
@@ -76,6 +79,9 @@ struct Dev {
     float sigma_f;
     int walls_move;       // nonzero: some non-periodic face moves
     const double *wallv;  // 6 x 3 face velocities (x-, x+, y-, y+, z-, z+)
+    // highest z-plane of a bulk tile holding liquid or interface cells: read
+    // (previous step) and written (this step) slots, swapped every step
+    int *ztop_rd, *ztop_wr;
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,

@@ -1038,6 +1038,8 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
 // consecutive z: grid (ceil(nx ny / BULK_THREADS), 1, ceil(nz / zb)).
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_body(const Dev &d, const VB &vb, int zb) {
+    // a tile above the previous step's fluid (plus a margin) holds only gas
+    if ((int)(vb.z * zb) > __ldg(d.ztop_rd) + ZTOP_MARGIN) return;
     const unsigned p = vb.x * BULK_THREADS + threadIdx.x;
     const bool in = p < (unsigned)d.nx * (unsigned)d.ny;
     const int y = in ? (int)(p / (unsigned)d.nx) : 0;
@@ -1143,6 +1145,9 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
 #pragma unroll
     for (int k = 0; k < ZBMAX; ++k)
         if (in && z0 + k < z1) fl |= (uint64_t)d.flags[i + k * sz] << (8 * k);
+    // record the highest tile holding liquid or interface cells (one atomic per warp)
+    if (__any_sync(0xffffffffu, (fl & 0x0303030303030303ull) != 0) && (threadIdx.x & 31) == 0)
+        atomicMax(d.ztop_wr, z1 - 1);
     if (fl == 0) return;
 #pragma unroll 1
     for (int z = z0; z < z1; ++z, i += sz) {
@@ -1231,6 +1236,8 @@ template <> struct Pipe<2> {
 
 template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_pipe(Dev d) {
+    // this variant visits every tile: record the grid's top so the next step skips none
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) atomicMax(d.ztop_wr, d.nz - 1);
     using P = Sto<S>;
     __shared__ uint32_t slots[2][Q][BULK_THREADS];
     const int tid = threadIdx.x;
@@ -1369,6 +1376,8 @@ __device__ __forceinline__ void stage_row(const Dev &d, char *stage, uint64_t *b
 
 template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_tma(Dev d) {
+    // this variant visits every tile: record the grid's top so the next step skips none
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) atomicMax(d.ztop_wr, d.nz - 1);
     using P = Sto<S>;
     using G = Stage<S>;
     extern __shared__ __align__(128) char smem[];
@@ -1518,6 +1527,9 @@ template <int S>
 __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
     using P = Sto<S>;
     const long long N = d.N;
+    // the bulk kernel has read this step's fluid top: clear the slot for the
+    // next step to record into
+    if (vb.x == 0 && threadIdx.x == 0) *d.ztop_rd = -1;
     uint32_t n = wl_count(d, WL_IFACE);
     for (uint32_t it = vb.x * blockDim.x + threadIdx.x; it < n; it += vb.nx * blockDim.x) {
         long long i = d.list[WL_IFACE][it];
@@ -1787,6 +1799,7 @@ __device__ __forceinline__ void conv_init_body(const Dev &d, const VB &vb) {
             long long i = d.list[WL_NEWG][it_a];
             int x, y, z;
             coords(d, i, x, y, z);
+            if (z > *d.ztop_wr + ZTOP_MARGIN) atomicOr(d.status, ST_TOP);
             double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
             int cnt = 0;
 #pragma unroll 1
@@ -2176,6 +2189,7 @@ __device__ __forceinline__ void remap_resolve_body(const Dev &d, const VB &vb) {
             if (dec == CL_G) continue;
             int x, y, z;
             coords(d, i, x, y, z);
+            if (z > *d.ztop_wr + ZTOP_MARGIN) atomicOr(d.status, ST_TOP);
             double p[3] = {x + 0.5, y + 0.5, z + 0.5}, uw[3];
             body_velocity_at(d, b, p, uw);
             double f[Q];

@@ -213,3 +213,22 @@ def test_neighbour_conversion_rule_parity(fill_value):
 
     g, o, gb, ob, gs, ref = run_both(T._pool_with_cell(I.INTERFACE, fill_value), 20, storage="f64")
     assert_f64_parity(g, o, gb, ob)
+
+
+def test_rising_droplet_crosses_skipped_tiles():
+    """A droplet launched upward through an all-gas column: the bulk kernel
+    skips tiles above the previous step's fluid top, so the drop rising by
+    many planes checks that the tracked top follows it (F64 parity after 300
+    steps, the top plane risen by at least 8 cells, no error status)."""
+    n, nz = 16, 40
+    drop = I.droplet(n, 4.0, sigma=0.0, seed_offset=(8.0, 8.0, 6.0))
+    pad = (nz - n) * n * n
+    flags = np.concatenate([drop.flags, np.full(pad, I.GAS, np.uint8)])
+    fill = np.concatenate([drop.fill, np.zeros(pad)])
+    sc = dataclasses.replace(drop, name="rising_droplet", nz=nz, flags=flags, fill=fill, rho=np.ones(n * n * nz),
+                             vel=np.tile([0.0, 0.0, 0.05], n * n * nz))
+    g, o, gb, ob, gs, _ = run_both(sc, 300, chunks=3)
+    assert gs["status"] == 0
+    assert_f64_parity(g, o, gb, ob)
+    fluid_z = np.nonzero((g["flags"] == I.LIQUID) | (g["flags"] == I.INTERFACE))[0] // (n * n)
+    assert fluid_z.max() >= 10 + 8, fluid_z.max()
