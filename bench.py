@@ -354,6 +354,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tank sweep")
+    ap.add_argument("--batch-tanks", type=int, default=64, help="tanks of the batched sweep (small profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end run (default: the workload's job length)")
     args = ap.parse_args()
     ws, rank, local = dist_info()
@@ -399,7 +400,7 @@ def main():
     if not args.no_variants and not args.no_batch:
         from paper_1201_0351_gb300 import inputs
 
-        batch = run_batch(inputs.batched_sweep_tanks(64), "f16s", args.steps, max(args.warmup, 3), 5,
+        batch = run_batch(inputs.batched_sweep_tanks(args.batch_tanks), "f16s", args.steps, max(args.warmup, 3), 5,
                           barrier=barrier)
     n = sc.nx * sc.ny * sc.nz
     ms, value = whole_job(main_run["ms_total"], n, args.steps, ws, "cuda")

@@ -72,6 +72,12 @@ constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2
 #ifndef LBMFS_BULK_PIPE_ZB
 #define LBMFS_BULK_PIPE_ZB 16  // z-planes per block of the software-pipelined bulk kernel
 #endif
+#ifndef LBMFS_FORCE_MINB
+#define LBMFS_FORCE_MINB 3  // resident 256-thread blocks per SM of the float-storage force kernel
+#endif
+#ifndef LBMFS_FORCE_ROWS
+#define LBMFS_FORCE_ROWS 1  // range rows per warp in the float-storage force kernel
+#endif
 #ifndef LBMFS_IFACE_MINB
 #define LBMFS_IFACE_MINB 4  // resident blocks per SM asked of ptxas for the interface kernel (128 registers)
 #endif
@@ -763,8 +769,26 @@ __device__ __forceinline__ void nb_update_body(const Dev &d, const VB &vb) {
 __global__ void k_nb_update(const __grid_constant__ Dev d) { nb_update_body(d, vb_own()); }
 
 // ---- C4: momentum exchange at the links into body vb.y (state at t)
+// Fixed-point sums of the float storages' per-cell force remainders: v * 2^s
+// rounded to nearest (ties away from zero), built from the float's bits with
+// integer operations (no double arithmetic; integer sums are exact, so the
+// block and body totals do not depend on the order of the cells).
+// |v| >= 2^(38 - s) saturates.
+constexpr int FX_FORCE = 32, FX_TORQUE = 30;
+__device__ __forceinline__ long long fixed_point(float v, int s) {
+    const unsigned b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + s;  // |v| 2^s = m 2^sh for normal numbers
+    long long r;
+    if (e == 0 || sh < -25) r = 0;
+    else if (sh < 0) r = (m + (1ll << (-sh - 1))) >> -sh;
+    else r = sh > 38 ? (1ll << 62) : (m << sh);
+    return (b >> 31) ? -r : r;
+}
+
 template <int S>
-__device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
+__device__ __forceinline__ void forces_f64_body(const Dev &d, const VB &vb) {
     int bi = vb.y;
     const Body &b = d.bodies[bi];
     int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, b.lo[2] - 1};
@@ -779,11 +803,6 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
         }
     }
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    long long ik[3] = {0, 0, 0}, it[3] = {0, 0, 0};  // exact gas-pressure sums (float storages)
-    // body state in float for the float storages, rounded once per thread
-    const float of[3] = {(float)b.o[0], (float)b.o[1], (float)b.o[2]};
-    const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
-    const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
     // the cells of the box around the body spread over all the body's blocks
     // (a fixed cell-to-thread map: the sums below stay deterministic); only
     // cells next to an obstacle (neighbour-obstacle bit) can hold links
@@ -796,7 +815,7 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
         int fb = d.flags[i];
         int cl = fb & CL_MASK;
         if (!(fb & NB_OBST) || cl == CL_O) continue;
-        if constexpr (S == 0) {
+        {
             // double, in the order of the plain restatement
             const double phi_x = cl == CL_L ? 1.0 : (cl == CL_I ? d.phisrc[i] : 0.0);
             const double r[3] = {min_image(d, (x + 0.5) - b.o[0], 0), min_image(d, (y + 0.5) - b.o[1], 1),
@@ -837,32 +856,132 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                 acc[5] += r[0] * F1 - r[1] * F0;
                 acc[6] += fabs(g);
             }
-        } else {
-            // reduced-precision storage: the link term is split into the
-            // uniform gas-pressure part 2 w_q rho_G (double) and the small
-            // remainder 2 (phi (f_qbar - w_q rho_G) + moving-wall part),
-            // computed in float from the stored deviations f - w.  The
-            // lever arm r is the cell's, so each part is summed over the
-            // cell's links first and its torque is r x that sum.
-            // Directions into body bi: all neighbour classes requested
-            // at once, then the body ids of the obstacle directions.
-            unsigned om = 0, lm = 0;
+        }
+    }
+    // deterministic block reduction (fixed shuffle tree, then warps in order);
+    // a warp without any link skips the tree (its sums are exact zeros)
+    __shared__ double sh[8][7];
+    int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    int lane = tid & 31, wid = tid >> 5;
+    const bool any = __any_sync(0xffffffffu, acc[6] != 0.0 || acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double v = acc[c];
+        if (any)
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[wid][c] = v;
+    }
+    __syncthreads();
+    if (tid < 7) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sh[w][tid];
+        d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = v;
+    }
+}
+
+// Sum of a 64-bit integer over the 32 lanes of a warp: three limbs (bits
+// 0-20, 21-41 and the signed rest) summed by warp reductions, whose 32-lane
+// sums stay within 32 bits for |v| < 2^62.
+__device__ __forceinline__ long long warp_sum64(long long v) {
+    const unsigned c = (unsigned)(v & 0x1fffffll), b = (unsigned)((v >> 21) & 0x1fffffll);
+    const int a = (int)(v >> 42);
+    const unsigned sc = __reduce_add_sync(0xffffffffu, c), sb = __reduce_add_sync(0xffffffffu, b);
+    const int sa = __reduce_add_sync(0xffffffffu, a);
+    return (long long)sa * (1ll << 42) + (long long)sb * (1ll << 21) + (long long)sc;
+}
+
+// Float storages.  The rows (y, z) of the cell range around the body are
+// spread over the body's warps, lanes along x (coalesced flag loads, no
+// per-cell division); every sum is an integer, so the totals do not depend
+// on that mapping.  The link term is split into the uniform gas-pressure part
+// 2 w_q rho_G (exact integer sums of 36 (2 w_q) c_qbar and of the lever arm
+// twice the cell centre) and the small remainder 2 (phi (f_qbar - w_q rho_G)
+// + moving-wall part), computed in float from the stored deviations f - w and
+// summed in fixed point.  The lever arm r is the cell's, so each part is
+// summed over the cell's links first and its torque is r x that sum.
+template <int S>
+__device__ __forceinline__ void forces_float_body(const Dev &d, const VB &vb) {
+    const int bi = vb.y;
+    const Body &b = d.bodies[bi];
+    int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, b.lo[2] - 1};
+    int hi[3] = {b.hi[0] + 1, b.hi[1] + 1, b.hi[2] + 1};
+    const int n3[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        if (!(d.periodic & (1u << k))) {
+            lo[k] = lo[k] < 0 ? 0 : lo[k];
+            hi[k] = hi[k] > n3[k] ? n3[k] : hi[k];
+        } else if (hi[k] - lo[k] > n3[k]) {
+            hi[k] = lo[k] + n3[k];
+        }
+    }
+    long long ia[7] = {0, 0, 0, 0, 0, 0, 0};         // fixed-point remainder sums
+    long long ik[3] = {0, 0, 0}, it[3] = {0, 0, 0};  // exact gas-pressure sums
+    bool hit = false;
+    // body state in float, rounded once per thread
+    const float of[3] = {(float)b.o[0], (float)b.o[1], (float)b.o[2]};
+    const float vf[3] = {(float)b.v[0], (float)b.v[1], (float)b.v[2]};
+    const float wfv[3] = {(float)b.w[0], (float)b.w[1], (float)b.w[2]};
+    const float rg = (float)d.rho_g, wrg1 = d.rg1_f;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5, nwarp = (blockDim.x * blockDim.y) >> 5;
+    const int lx = hi[0] - lo[0];
+    const unsigned ly = (unsigned)(hi[1] - lo[1]), nrows = ly * (unsigned)(hi[2] - lo[2]);
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    // as many of the body's blocks as give each warp LBMFS_FORCE_ROWS rows;
+    // the others contribute zeros
+    const unsigned per_block = (unsigned)nwarp * LBMFS_FORCE_ROWS;
+    const unsigned used = min((unsigned)vb.nx, (nrows + per_block - 1) / per_block);
+    if ((unsigned)vb.x >= used) {
+        if (tid < 7) d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = 0.0;
+        return;
+    }
+    for (unsigned row = (unsigned)vb.x * nwarp + wid; row < nrows; row += used * nwarp) {
+        int y = lo[1] + (int)(row % ly), z = lo[2] + (int)(row / ly);
+        if (y < 0 || y >= d.ny) y = ((y % d.ny) + d.ny) % d.ny;  // only periodic axes leave [0, n)
+        if (z < 0 || z >= d.nz) z = ((z % d.nz) + d.nz) % d.nz;
+        for (int xo = lane; xo < lx; xo += 32) {
+            int x = lo[0] + xo;
+            if (x < 0 || x >= d.nx) x = ((x % d.nx) + d.nx) % d.nx;
+            const long long i = x + sy * (y + (long long)d.ny * z);
+            const int fb = d.flags[i];
+            const int cl = fb & CL_MASK;
+            if (!(fb & NB_OBST) || cl == CL_O) continue;
+            // directions into body bi: all neighbour classes requested at
+            // once (linear offsets away from the grid faces), then the body
+            // ids of the obstacle directions
+            const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+            // a liquid or interface cell's link terms read its populations:
+            // requested together with the neighbour classes
+            float fc[Q];
+            if (cl != CL_G) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) fc[q] = Sto<S>::ld(d.fsrc, q, i, d.N);
+            }
+            unsigned om = 0;
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                const long long si = inner ? i - (cx(q) + cy(q) * sy + cz(q) * sz)
+                                           : nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
                 if (si >= 0 && clsv(d, si) == CL_O) om |= 1u << q;
             }
+            unsigned lm = om;  // with one body every obstacle cell is its
+            if (d.nb > 1) {
+                lm = 0;
 #pragma unroll
-            for (int q = 1; q < Q; ++q)
-                if (om & (1u << q))
-                    if (d.bid[nbr(d, x, y, z, -cx(q), -cy(q), -cz(q))] == bi) lm |= 1u << q;
+                for (int q = 1; q < Q; ++q)
+                    if (om & (1u << q)) {
+                        const long long si = inner ? i - (cx(q) + cy(q) * sy + cz(q) * sz)
+                                                   : nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                        if (d.bid[si] == bi) lm |= 1u << q;
+                    }
+            }
             if (!lm) continue;
+            hit = true;
             const float phf = cl == CL_L ? 1.0f : (cl == CL_I ? (float)d.phisrc[i] : 0.0f);
-            const float rg = (float)d.rho_g, wrg1 = d.rg1_f;
             // lever arm from the cell centre (minimum image on periodic
             // axes): float for the small remainder, and twice the cell
             // centre as an integer for the exact gas-pressure part
-            const int xyz[3] = {x, y, z}, nn[3] = {d.nx, d.ny, d.nz};
+            const int xyz[3] = {x, y, z};
             float rf[3];
             long long c2[3];
 #pragma unroll
@@ -870,9 +989,9 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                 int xk = xyz[k];
                 rf[k] = ((float)xk + 0.5f) - of[k];
                 if (d.periodic & (1u << k)) {
-                    const int sh = (int)floorf(rf[k] / (float)nn[k] + 0.5f);
-                    xk -= sh * nn[k];
-                    rf[k] -= (float)(sh * nn[k]);
+                    const int shn = (int)floorf(rf[k] / (float)n3[k] + 0.5f);
+                    xk -= shn * n3[k];
+                    rf[k] -= (float)(shn * n3[k]);
                 }
                 c2[k] = 2ll * xk + 1;
             }
@@ -887,8 +1006,7 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                 float gdev = 0.0f;
                 if (cl != CL_G) {
                     // u_w at the link midpoint, r + c_qbar / 2 from the body centre
-                    const float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb),
-                                pz = rf[2] + 0.5f * cz(qb);
+                    const float px = rf[0] + 0.5f * cx(qb), py = rf[1] + 0.5f * cy(qb), pz = rf[2] + 0.5f * cz(qb);
                     const float ux = vf[0] + (wfv[1] * pz - wfv[2] * py);
                     const float uy = vf[1] + (wfv[2] * px - wfv[0] * pz);
                     const float uz = vf[2] + (wfv[0] * py - wfv[1] * px);
@@ -898,12 +1016,12 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                         if (rho_x < 0.0f) {
                             float dr = 0.0f;
 #pragma unroll
-                            for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
+                            for (int k = 0; k < Q; ++k) dr += fc[k];
                             rho_x = 1.0f + dr;
                         }
                         C = phf * (3.0f * wf(q) * rho_x * cuw);
                     }
-                    const float dev = Sto<S>::ld(d.fsrc, qb, i, d.N) + wf(q) * wrg1;
+                    const float dev = fc[qb] + wf(q) * wrg1;
                     gdev = 2.0f * (phf * dev + C);
                 }
                 if (cx(qb)) {
@@ -920,16 +1038,15 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
                 }
                 fabs_sum += fabsf((float)m36 * (rg * (1.0f / 36.0f)) + gdev);
             }
-            // remainder: the cell's links in float, cells in double
-            acc[0] += (double)gx;
-            acc[1] += (double)gy;
-            acc[2] += (double)gz;
-            acc[3] += (double)(rf[1] * gz - rf[2] * gy);
-            acc[4] += (double)(rf[2] * gx - rf[0] * gz);
-            acc[5] += (double)(rf[0] * gy - rf[1] * gx);
-            acc[6] += (double)fabs_sum;
-            // gas-pressure part (rho_G / 36) K, exactly in integers:
-            // its torque is (rho_G / 36) (sum c2 x K / 2 - o x sum K)
+            ia[0] += fixed_point(gx, FX_FORCE);
+            ia[1] += fixed_point(gy, FX_FORCE);
+            ia[2] += fixed_point(gz, FX_FORCE);
+            ia[3] += fixed_point(rf[1] * gz - rf[2] * gy, FX_TORQUE);
+            ia[4] += fixed_point(rf[2] * gx - rf[0] * gz, FX_TORQUE);
+            ia[5] += fixed_point(rf[0] * gy - rf[1] * gx, FX_TORQUE);
+            ia[6] += fixed_point(fabs_sum, FX_FORCE);
+            // gas-pressure part (rho_G / 36) K: its torque is
+            // (rho_G / 36) (sum c2 x K / 2 - o x sum K)
             ik[0] += kx;
             ik[1] += ky;
             ik[2] += kz;
@@ -938,57 +1055,52 @@ __device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
             it[2] += c2[0] * ky - c2[1] * kx;
         }
     }
-    // deterministic block reduction (fixed shuffle tree, then warps in order);
-    // a warp without any link skips the tree (its sums are exact zeros)
-    __shared__ double sh[8][7];
-    int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    int lane = tid & 31, wid = tid >> 5;
-    const bool any = __any_sync(0xffffffffu, acc[6] != 0.0 || acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0);
+    // warp sums, then the warps' sums in the block (integers: exact); a warp
+    // without any link skips the reductions (its sums are zeros)
+    __shared__ long long shi[8][13];
+    const bool any = __any_sync(0xffffffffu, hit);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-        double v = acc[c];
-        if (any)
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[wid][c] = v;
-    }
-    __shared__ long long shi[8][6];
-    if constexpr (S != 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            long long v = c < 3 ? ik[c] : it[c - 3];
-            if (any)
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) shi[wid][c] = v;
-        }
+    for (int c = 0; c < 13; ++c) {
+        long long v = c < 7 ? ia[c] : (c < 10 ? ik[c - 7] : it[c - 10]);
+        if (any) v = warp_sum64(v);
+        if (lane == 0) shi[wid][c] = any ? v : 0ll;
     }
     __syncthreads();
     if (tid < 7) {
-        double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += sh[w][tid];
-        if constexpr (S != 0) {
-            if (tid < 6) {
-                long long K[3] = {0, 0, 0}, T2[3] = {0, 0, 0};
-                for (int w = 0; w < 8; ++w)
-                    for (int k = 0; k < 3; ++k) {
-                        K[k] += shi[w][k];
-                        T2[k] += shi[w][3 + k];
-                    }
-                const double g36 = d.rho_g / 36.0;
-                if (tid < 3) {
-                    v += g36 * (double)K[tid];
-                } else {
-                    const int k = tid - 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-                    // (sum c2 x K) / 2 - o x sum K, component k
-                    const double ox = b.o[k1] * (double)K[k2] - b.o[k2] * (double)K[k1];
-                    v += g36 * (0.5 * (double)T2[k] - ox);
+        long long I = 0;
+        for (int w = 0; w < nwarp; ++w) I += shi[w][tid];
+        double v = (double)I * (tid >= 3 && tid < 6 ? 1.0 / (double)(1ll << FX_TORQUE) : 1.0 / (double)(1ll << FX_FORCE));
+        if (tid < 6) {
+            long long K[3] = {0, 0, 0}, T2[3] = {0, 0, 0};
+            for (int w = 0; w < nwarp; ++w)
+                for (int k = 0; k < 3; ++k) {
+                    K[k] += shi[w][7 + k];
+                    T2[k] += shi[w][10 + k];
                 }
+            const double g36 = d.rho_g / 36.0;
+            if (tid < 3) {
+                v += g36 * (double)K[tid];
+            } else {
+                const int k = tid - 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                // (sum c2 x K) / 2 - o x sum K, component k
+                const double ox = b.o[k1] * (double)K[k2] - b.o[k2] * (double)K[k1];
+                v += g36 * (0.5 * (double)T2[k] - ox);
             }
         }
         d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = v;
     }
 }
+
 template <int S>
-__global__ void __launch_bounds__(256, 2) k_forces(const __grid_constant__ Dev d) { forces_body<S>(d, vb_own()); }
+__device__ __forceinline__ void forces_body(const Dev &d, const VB &vb) {
+    if constexpr (S == 0) forces_f64_body<S>(d, vb);
+    else forces_float_body<S>(d, vb);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256, S == 0 ? 2 : LBMFS_FORCE_MINB) k_forces(const __grid_constant__ Dev d) {
+    forces_body<S>(d, vb_own());
+}
 
 // Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
 // an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
@@ -2338,7 +2450,7 @@ struct BkReset {
         if (threadIdx.x < WL_COUNT) d.cnt[threadIdx.x] = 0;
     }
 };
-template <int S> LBMFS_BATCH_BODY(BkForces, 256, 2, forces_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, forces_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, 8>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
