@@ -2435,23 +2435,30 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB)
         const Tile e = table[t];
         const VB vb{e.x, e.y, e.z, e.nx, e.ny, e.nz};
         K::run(ts.d[e.tank], vb, zb);
-        __syncthreads();  // the next entry's body reuses this one's shared memory
+        // the next entry's body reuses this one's shared memory; bodies
+        // without shared memory let a block's warps move on independently
+        if constexpr (K::SMEM) __syncthreads();
     }
 }
 
-#define LBMFS_BATCH_BODY(NAME, THR, MB, CALL)                                                 \
+#define LBMFS_BATCH_BODY_SM(NAME, THR, MB, SM, CALL)                                          \
     struct NAME {                                                                              \
         static constexpr int THREADS = THR, MINB = MB;                                         \
+        static constexpr bool SMEM = SM;                                                       \
         static __device__ __forceinline__ void run(const Dev &d, const VB &vb, int zb) { CALL; } \
     };
+#define LBMFS_BATCH_BODY(NAME, THR, MB, CALL) LBMFS_BATCH_BODY_SM(NAME, THR, MB, false, CALL)
 struct BkReset {
     static constexpr int THREADS = 32, MINB = 1;
+    static constexpr bool SMEM = false;
     static __device__ __forceinline__ void run(const Dev &d, const VB &, int) {
         if (threadIdx.x < WL_COUNT) d.cnt[threadIdx.x] = 0;
     }
 };
-template <int S> LBMFS_BATCH_BODY(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, forces_body<S>(d, vb))
-template <int S> LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, 8>(d, vb, zb)))
+template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, true, forces_body<S>(d, vb))
+// one instantiation per z-planes-per-tile choice (the column loop unrolled to it)
+template <int S, int ZB>
+LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, ZB>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
@@ -2463,13 +2470,22 @@ template <int S> LBMFS_BATCH_BODY(BkConvFinish, LIST_THREADS, 1, conv_finish_bod
 LBMFS_BATCH_BODY(BkBodies, 32, 1, bodies_body(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkRemapCover, 256, 1, remap_cover_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkRemapPending, 256, 1, remap_pending_body(d, vb))
-template <int S> LBMFS_BATCH_BODY(BkRemapResolve, REMAP_THREADS, 1, remap_resolve_body<S>(d, vb))
+template <int S> LBMFS_BATCH_BODY_SM(BkRemapResolve, REMAP_THREADS, 1, true, remap_resolve_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkNbUpdate, LIST_THREADS, 1, nb_update_body(d, vb))
 #undef LBMFS_BATCH_BODY
+#undef LBMFS_BATCH_BODY_SM
 
 template <class K> void batch_launch(const BatchLaunch &b, int sh, dim3 block, cudaStream_t st) {
     const Shape &x = b.sh[sh];
     if (x.n) k_batch<K><<<x.grid, block, 0, st>>>(*b.ts, x.table, x.n, b.zb);
+}
+template <int S> void batch_bulk_launch(const BatchLaunch &b, cudaStream_t st) {
+    switch (b.zb) {
+    case 1: batch_launch<BkLiquid<S, 1>>(b, SH_BULK, BULK_THREADS, st); break;
+    case 2: batch_launch<BkLiquid<S, 2>>(b, SH_BULK, BULK_THREADS, st); break;
+    case 4: batch_launch<BkLiquid<S, 4>>(b, SH_BULK, BULK_THREADS, st); break;
+    default: batch_launch<BkLiquid<S, 8>>(b, SH_BULK, BULK_THREADS, st); break;
+    }
 }
 
 template <int S> struct Launch {
@@ -2566,7 +2582,7 @@ template <int S> struct BatchStep {
         mark();
         batch_launch<BkForces<S>>(b, SH_FORCE, dim3(32, 8), st);
         mark();
-        batch_launch<BkLiquid<S>>(b, SH_BULK, BULK_THREADS, st);
+        batch_bulk_launch<S>(b, st);
         mark();
         batch_launch<BkInterface<S>>(b, SH_IFACE, 128, st);
         mark();
@@ -2600,10 +2616,10 @@ template <int S> struct BatchStep {
         for (int sh : shapes) n += b.sh[sh].n ? 1 : 0;
         return n;
     }
-    static void bulk(const BatchLaunch &b, cudaStream_t st) { batch_launch<BkLiquid<S>>(b, SH_BULK, BULK_THREADS, st); }
+    static void bulk(const BatchLaunch &b, cudaStream_t st) { batch_bulk_launch<S>(b, st); }
     static int bulk_blocks_per_sm() {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BkLiquid<S>>, BULK_THREADS, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<BkLiquid<S, 4>>, BULK_THREADS, 0) != cudaSuccess)
             return 1;
         return nb > 0 ? nb : 1;
     }
