@@ -128,6 +128,11 @@ template <> struct Sto<0> {
         for (int q = 0; q < Q; ++q) st(g, q, i, N, f[q]);
     }
     static size_t bytes(long long N) { return (size_t)N * Q * sizeof(double); }
+    static constexpr int SCALE = 1;
+    static __device__ __forceinline__ double ld_raw(const void *g, int q, long long i, long long N) { return ld(g, q, i, N); }
+    static __device__ __forceinline__ double ldg_raw(const void *g, int q, long long i, long long N) {
+        return ldg(g, q, i, N);
+    }
 };
 
 template <> struct Sto<1> {
@@ -167,6 +172,13 @@ template <> struct Sto<1> {
     static __device__ __forceinline__ float st_one(void *g, int q, long long i, long long N, float v) {
         st(g, q, i, N, v);
         return v;
+    }
+    // values as stored (no scale)
+    static constexpr int SCALE = 1;
+    static __device__ __forceinline__ float ld_raw(const void *g, int q, long long i, long long N) { return ld(g, q, i, N); }
+    static __device__ __forceinline__ float ldg_raw(const void *g, int q, long long i, long long N) { return ldg(g, q, i, N); }
+    static __device__ __forceinline__ float st_raw(void *g, int q, long long i, long long N, float v) {
+        return st_one(g, q, i, N, v);
     }
 };
 
@@ -218,6 +230,25 @@ template <> struct Sto<2> {
         __half hq = __float2half_rn(v * F16_SCALE);
         pop_st(const_cast<__half *>(hp(g, N)) + ((long long)(q - 1) * N + i), hq);
         return __half2float(hq) * F16_INV_SCALE;
+    }
+    // values as stored: q >= 1 times F16_SCALE, the rest population unscaled
+    static constexpr int SCALE = (int)F16_SCALE;
+    static __device__ __forceinline__ float ld_raw(const void *g, int q, long long i, long long N) {
+        if (q == 0) return pop_ld(reinterpret_cast<const float *>(g) + i);
+        return __half2float(pop_ld(hp(g, N) + ((long long)(q - 1) * N + i)));
+    }
+    static __device__ __forceinline__ float ldg_raw(const void *g, int q, long long i, long long N) {
+        if (q == 0) return pop_ldg(reinterpret_cast<const float *>(g) + i);
+        return __half2float(pop_ldg(hp(g, N) + ((long long)(q - 1) * N + i)));
+    }
+    static __device__ __forceinline__ float st_raw(void *g, int q, long long i, long long N, float v) {
+        if (q == 0) {
+            pop_st(reinterpret_cast<float *>(g) + i, v);
+            return v;
+        }
+        __half hq = __float2half_rn(v);
+        pop_st(const_cast<__half *>(hp(g, N)) + ((long long)(q - 1) * N + i), hq);
+        return __half2float(hq);
     }
 };
 
@@ -524,11 +555,18 @@ __device__ __forceinline__ float collide_f(const Dev &d, const float *dp, float 
 // population in exact arithmetic, it makes the stored cell sum equal the
 // streamed-in sum up to one rounding (no mass drift from float rounding).
 // Returns the collision density.
-template <class Store>
+//
+// SC (a power of two): dp_q for q >= 1 arrive, and are stored, multiplied by
+// SC (the FP16 storage's own scale), dp_0 unscaled.  Every intermediate that
+// carries a population is then SC times the unscaled one; scaling by a power
+// of two adds no rounding, so this is the unscaled collision without a
+// multiplication per load and per store.
+template <int SC = 1, class Store>
 __device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, Store store) {
-    float dr = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+    constexpr float sc = (float)SC, isc = 1.0f / (float)SC;
+    float dr = dp[0], j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) dr += dp[q];
+    for (int q = 1; q < Q; ++q) dr = fmaf(dp[q], isc, dr);  // exact product: dr + dp_q / SC, one rounding
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (cx(q)) j0 += cx(q) * dp[q];
@@ -537,14 +575,14 @@ __device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, 
     }
     const float rho = 1.0f + dr;
     const float inv = 1.0f / rho;
-    const float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
+    const float ux = (j0 * inv) * isc, uy = (j1 * inv) * isc, uz = (j2 * inv) * isc;
     const float usq = ux * ux + uy * uy + uz * uz;
     const float om = d.omega_f, om1 = 1.0f - om;
     const float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
     const float ua3 = 3.0f * (ux * ax + uy * ay + uz * az);
     // per weight class: w dr, w rho, 3 w rho
-    const float wdr1 = wf(1) * dr, wr1 = wf(1) * rho, wr13 = 3.0f * wr1;
-    const float wdr2 = wf(7) * dr, wr2 = wf(7) * rho, wr23 = 3.0f * wr2;
+    const float wdr1 = (wf(1) * dr) * sc, wr1 = (wf(1) * rho) * sc, wr13 = 3.0f * wr1;
+    const float wdr2 = (wf(7) * dr) * sc, wr2 = (wf(7) * rho) * sc, wr23 = 3.0f * wr2;
     float rest = 0.0f;
     // opposite directions q, qbar share everything but the sign of c.u and
     // c.a: f_eq - w = A +- B, force term = C +- D with
@@ -569,7 +607,7 @@ __device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, 
         rest += dp[q] - store(q, dn);
         rest += dp[qb] - store(qb, dnb);
     }
-    store(0, dp[0] + rest);
+    store(0, dp[0] + rest * isc);
     return rho;
 }
 
@@ -1179,10 +1217,20 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         }
         if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
     } else {
+        // fp in the storage's raw units (to_raw)
         void *g = d.fdst;
         const long long N = d.N;
-        float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st_one(g, q, i, N, v); });
+        float rho = collide_store_f<P::SCALE>(d, fp, [&](int q, float v) { return P::st_raw(g, q, i, N, v); });
         if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+    }
+}
+
+// populations gathered as values into the storage's raw units (q >= 1 times
+// the FP16 storage's scale; exact)
+template <int S> __device__ __forceinline__ void to_raw(typename Sto<S>::R *fp) {
+    if constexpr (S == 2) {
+#pragma unroll
+        for (int q = 1; q < Q; ++q) fp[q] *= F16_SCALE;
     }
 }
 
@@ -1214,6 +1262,7 @@ template <int S>
 __device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
     typename Sto<S>::R fp[Q];
     gather_general<S>(d, x, y, z, i, fp);
+    to_raw<S>(fp);
     collide_store<S>(d, fp, i);
 }
 
@@ -1234,10 +1283,11 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
         const long long N = d.N;
         const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
 #pragma unroll
-        for (int q = 1; q < Q; ++q) fp[q] = P::ld(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
-        fp[0] = P::ld(d.fsrc, 0, i, N);
+        for (int q = 1; q < Q; ++q) fp[q] = P::ld_raw(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
+        fp[0] = P::ld_raw(d.fsrc, 0, i, N);
     } else {
         gather_general<S>(d, x, y, z, i, fp);
+        to_raw<S>(fp);
     }
     collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
 }
@@ -1272,8 +1322,8 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
             // no obstacle or wall in the neighbourhood and a liquid cell never
             // touches gas: plain pull from the 18 neighbours
 #pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = P::ldg(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
-            fp[0] = P::ldg(d.fsrc, 0, i, N);
+            for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
         } else if (c == CL_L && !d.periodic && !d.walls_move) {
             // on a face of a grid without periodic axes, no obstacle
             // neighbour: a source beyond a face is a resting wall, which
@@ -1284,19 +1334,21 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
             for (int q = 1; q < Q; ++q) {
                 const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
                                  (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
-                fp[q] = out ? P::ldg(d.fsrc, opp(q), i, N) : P::ldg(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+                fp[q] = out ? P::ldg_raw(d.fsrc, opp(q), i, N)
+                            : P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
             }
-            fp[0] = P::ldg(d.fsrc, 0, i, N);
+            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
         } else if (c == CL_L && !d.walls_move) {
             // on a face with periodic axes: pull across the seams, walls as above
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                fp[q] = si >= 0 ? P::ldg(d.fsrc, q, si, N) : P::ldg(d.fsrc, opp(q), i, N);
+                fp[q] = si >= 0 ? P::ldg_raw(d.fsrc, q, si, N) : P::ldg_raw(d.fsrc, opp(q), i, N);
             }
-            fp[0] = P::ldg(d.fsrc, 0, i, N);
+            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
         } else {
             gather_general<S>(d, x, y, z, i, fp);
+            to_raw<S>(fp);
         }
         collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
     }
@@ -1387,6 +1439,7 @@ __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_pipe(D
 #pragma unroll
             for (int q = 0; q < Q; ++q)
                 fp[q] = Pipe<S>::get(&slots[b][0][tid], q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), d.N);
+            to_raw<S>(fp);
             collide_store<S>(d, fp, i);
         } else if ((fl_cur & CL_MASK) == CL_L) {
             liquid_cell_general<S>(d, x, y, z, i);
@@ -1537,10 +1590,8 @@ __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_tma(De
             float fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fp[q] = G::get(stage, q, tid + ((S == 2 && q > 0) ? Stage<2>::H : 4) - cx(q));
-            void *g = d.fdst;
-            const long long N = d.N;
-            float rho = collide_store_f(d, fp, [&](int q, float v) { return P::st_one(g, q, i, N, v); });
-            if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+            to_raw<S>(fp);
+            collide_store<S>(d, fp, i);
         } else if ((c & CL_MASK) == CL_L) {
             liquid_cell_general<S>(d, x, y, z, i);
         }
