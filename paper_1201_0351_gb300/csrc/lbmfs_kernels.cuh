@@ -736,7 +736,7 @@ __device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
     int x, y, z;
     coords(d, i, x, y, z);
     bool nb = false;
-#pragma unroll 1
+#pragma unroll
     for (int q = 1; q < Q; ++q) {
         int c = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
         nb = nb || c == CL_O;
@@ -796,12 +796,24 @@ __device__ __forceinline__ void nb_refresh_around(const Dev &d, long long i) {
     }
 }
 
+// one thread per (listed cell, direction): the cell itself (q = 0) or its
+// neighbour in direction q; cells refreshed twice get the same value (the
+// classes do not change in this kernel)
 __device__ __forceinline__ void nb_update_body(const Dev &d, const VB &vb) {
-    {
-        LIST_LOOP(WL_COVER, a) nb_refresh_around(d, d.list[WL_COVER][it_a]);
-    }
-    {
-        LIST_LOOP(WL_PEND, b) nb_refresh_around(d, d.list[WL_PEND][it_b]);
+    const uint32_t nc = wl_count(d, WL_COVER), np = wl_count(d, WL_PEND);
+    const unsigned long long n = (unsigned long long)(nc + np) * Q;
+    for (unsigned long long it = (unsigned long long)vb.x * blockDim.x + threadIdx.x; it < n;
+         it += (unsigned long long)vb.nx * blockDim.x) {
+        const uint32_t e = (uint32_t)(it / Q);
+        const int q = (int)(it % Q);
+        const long long c = e < nc ? (long long)d.list[WL_COVER][e] : (long long)d.list[WL_PEND][e - nc];
+        long long t = c;
+        if (q > 0) {
+            int x, y, z;
+            coords(d, c, x, y, z);
+            t = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+        }
+        if (t >= 0) nb_refresh(d, t);
     }
 }
 __global__ void k_nb_update(const __grid_constant__ Dev d) { nb_update_body(d, vb_own()); }
@@ -1913,12 +1925,22 @@ __device__ __forceinline__ void conv_filled_body(const Dev &d, const VB &vb) {
         long long i = d.list[WL_FILLED][it_a];
         int x, y, z;
         coords(d, i, x, y, z);
-#pragma unroll 1
+        // classes and emptied marks requested at once (this kernel sets no
+        // emptied mark and changes no class)
+        unsigned em = 0, gm = 0;
+#pragma unroll
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
             if (yi < 0) continue;
-            if (d.cmark[yi] & MK_EMPTIED) mark_and(d, yi, MK_EMPTIED);
-            if (clsv(d, yi) == CL_G) {
+            if (d.cmark[yi] & MK_EMPTIED) em |= 1u << q;
+            if (clsv(d, yi) == CL_G) gm |= 1u << q;
+        }
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            if (!((em | gm) & (1u << q))) continue;
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            if (em & (1u << q)) mark_and(d, yi, MK_EMPTIED);
+            if (gm & (1u << q)) {
                 uint8_t old = mark_or(d, yi, MK_NEWG);
                 if (!(old & MK_NEWG)) {
                     uint32_t pos = atomicAdd(&d.cnt[WL_NEWG], 1u);
@@ -1938,10 +1960,17 @@ __device__ __forceinline__ void conv_emptied_body(const Dev &d, const VB &vb) {
         if (!(d.cmark[i] & MK_EMPTIED)) continue;
         int x, y, z;
         coords(d, i, x, y, z);
-#pragma unroll 1
+        // classes requested at once (this kernel changes marks only)
+        unsigned lm = 0;
+#pragma unroll
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            if (yi < 0 || clsv(d, yi) != CL_L) continue;
+            if (yi >= 0 && clsv(d, yi) == CL_L) lm |= 1u << q;
+        }
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            if (!(lm & (1u << q))) continue;
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
             uint8_t old = mark_or(d, yi, MK_NEWL);
             if (!(old & MK_NEWL)) {
                 uint32_t pos = atomicAdd(&d.cnt[WL_NEWL], 1u);
@@ -1965,11 +1994,17 @@ __device__ __forceinline__ void conv_init_body(const Dev &d, const VB &vb) {
             if (z > *d.ztop_wr + ZTOP_MARGIN) atomicOr(d.status, ST_TOP);
             double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
             int cnt = 0;
+            // classes requested at once, then the fluid neighbours in q order
+            unsigned fm = 0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const int zc = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
+                if (zc == CL_L || zc == CL_I) fm |= 1u << q;
+            }
 #pragma unroll 1
             for (int q = 1; q < Q; ++q) {
+                if (!(fm & (1u << q))) continue;
                 long long zi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                int zc = cls(d, zi);
-                if (zc != CL_L && zc != CL_I) continue;
                 double u[3];
                 double r = cell_rho_u<S>(d, d.fdst, zi, u);
                 sr += r;
@@ -2020,10 +2055,17 @@ __global__ void k_conv_flags(const __grid_constant__ Dev d) { conv_flags_body(d,
 __device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
     int x, y, z;
     coords(d, i, x, y, z);
-#pragma unroll 1
+    // classes requested at once (this kernel changes marks only)
+    unsigned im = 0;
+#pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-        if (yi < 0 || clsv(d, yi) != CL_I) continue;
+        if (yi >= 0 && clsv(d, yi) == CL_I) im |= 1u << q;
+    }
+#pragma unroll 1
+    for (int q = 1; q < Q; ++q) {
+        if (!(im & (1u << q))) continue;
+        long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
         uint8_t old = mark_or(d, yi, MK_RECV);
         if (!(old & MK_RECV)) {
             uint32_t pos = atomicAdd(&d.cnt[WL_RECV], 1u);
@@ -2051,7 +2093,7 @@ __device__ __forceinline__ int iface_neighbours(const Dev &d, long long i) {
     int x, y, z;
     coords(d, i, x, y, z);
     int k = 0;
-#pragma unroll 1
+#pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
         if (yi >= 0 && clsv(d, yi) == CL_I) k++;
@@ -2072,12 +2114,18 @@ __device__ __forceinline__ void conv_excess_body(const Dev &d, const VB &vb) {
         int x, y, z;
         coords(d, i, x, y, z);
         double acc = 0.0;
-#pragma unroll 1
+        // the neighbours' marks requested at once, then the converted ones in q order
+        uint8_t mks[Q];
+#pragma unroll
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            if (yi < 0) continue;
-            uint8_t mk = d.cmark[yi];
+            mks[q] = yi < 0 ? (uint8_t)0 : d.cmark[yi];
+        }
+#pragma unroll 1
+        for (int q = 1; q < Q; ++q) {
+            const uint8_t mk = mks[q];
             if (!(mk & (MK_FILLED | MK_EMPTIED))) continue;
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
             acc += excess<S>(d, yi, mk) / iface_neighbours(d, yi);
         }
         double m = d.m[i] + acc;
@@ -2307,10 +2355,18 @@ __device__ __forceinline__ void remap_resolve_body(const Dev &d, const VB &vb) {
             coords(d, i, x, y, z);
             int nL = 0, nI = 0, nG = 0;
             double sr = 0.0, sp = 0.0;
+            // marks and classes requested at once, then the neighbours in q order
+            uint8_t cs[Q];
+#pragma unroll
             for (int q = 1; q < Q; ++q) {
                 long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                if (yi < 0 || (d.cmark[yi] & MK_PEND) || clsv(d, yi) == CL_O) continue;
-                int c = clsv(d, yi);
+                cs[q] = (yi < 0 || (d.cmark[yi] & MK_PEND)) ? (uint8_t)0 : (uint8_t)clsv(d, yi);
+            }
+#pragma unroll 1
+            for (int q = 1; q < Q; ++q) {
+                const int c = cs[q];
+                if (c == 0 || c == CL_O) continue;
+                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
                 if (c == CL_L) {
                     nL++;
                     sr += cell_density<S>(d, d.fdst, yi);
