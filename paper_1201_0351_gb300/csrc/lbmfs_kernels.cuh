@@ -1920,6 +1920,29 @@ __global__ void __launch_bounds__(128, LBMFS_IFACE_MINB) k_interface(const __gri
 // ------------------------------------------------- C3: conversions (Sec. 2.2)
 
 // filled cells: emptied neighbours are kept; gas neighbours become interface
+// set mark `bit` on the neighbours of (x, y, z) in the direction mask m (the
+// atomics issued together) and append the cells whose bit was newly set to
+// worklist `list` (one reservation for all of them)
+__device__ __forceinline__ void mark_append(const Dev &d, int x, int y, int z, unsigned m, uint8_t bit, int list) {
+    if (!m) return;
+    unsigned nw = 0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+        if (m & (1u << q)) {
+            const uint8_t old = mark_or(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)), bit);
+            if (!(old & bit)) nw |= 1u << q;
+        }
+    if (!nw) return;
+    uint32_t pos = atomicAdd(&d.cnt[list], (uint32_t)__popc(nw));
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+        if (nw & (1u << q)) {
+            if (pos < d.cap) d.list[list][pos] = (uint32_t)nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            else atomicOr(d.status, ST_OVERFLOW);
+            ++pos;
+        }
+}
+
 __device__ __forceinline__ void conv_filled_body(const Dev &d, const VB &vb) {
     LIST_LOOP(WL_FILLED, a) {
         long long i = d.list[WL_FILLED][it_a];
@@ -1935,20 +1958,10 @@ __device__ __forceinline__ void conv_filled_body(const Dev &d, const VB &vb) {
             if (d.cmark[yi] & MK_EMPTIED) em |= 1u << q;
             if (clsv(d, yi) == CL_G) gm |= 1u << q;
         }
-#pragma unroll 1
-        for (int q = 1; q < Q; ++q) {
-            if (!((em | gm) & (1u << q))) continue;
-            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            if (em & (1u << q)) mark_and(d, yi, MK_EMPTIED);
-            if (gm & (1u << q)) {
-                uint8_t old = mark_or(d, yi, MK_NEWG);
-                if (!(old & MK_NEWG)) {
-                    uint32_t pos = atomicAdd(&d.cnt[WL_NEWG], 1u);
-                    if (pos < d.cap) d.list[WL_NEWG][pos] = (uint32_t)yi;
-                    else atomicOr(d.status, ST_OVERFLOW);
-                }
-            }
-        }
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if (em & (1u << q)) mark_and(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)), MK_EMPTIED);
+        mark_append(d, x, y, z, gm, MK_NEWG, WL_NEWG);
     }
 }
 __global__ void k_conv_filled(const __grid_constant__ Dev d) { conv_filled_body(d, vb_own()); }
@@ -1967,17 +1980,7 @@ __device__ __forceinline__ void conv_emptied_body(const Dev &d, const VB &vb) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
             if (yi >= 0 && clsv(d, yi) == CL_L) lm |= 1u << q;
         }
-#pragma unroll 1
-        for (int q = 1; q < Q; ++q) {
-            if (!(lm & (1u << q))) continue;
-            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            uint8_t old = mark_or(d, yi, MK_NEWL);
-            if (!(old & MK_NEWL)) {
-                uint32_t pos = atomicAdd(&d.cnt[WL_NEWL], 1u);
-                if (pos < d.cap) d.list[WL_NEWL][pos] = (uint32_t)yi;
-                else atomicOr(d.status, ST_OVERFLOW);
-            }
-        }
+        mark_append(d, x, y, z, lm, MK_NEWL, WL_NEWL);
     }
 }
 __global__ void k_conv_emptied(const __grid_constant__ Dev d) { conv_emptied_body(d, vb_own()); }
@@ -2051,42 +2054,46 @@ __device__ __forceinline__ void conv_flags_body(const Dev &d, const VB &vb) {
 }
 __global__ void k_conv_flags(const __grid_constant__ Dev d) { conv_flags_body(d, vb_own()); }
 
-// interface neighbours of converted cells receive excess mass
-__device__ __forceinline__ void claim_receivers(const Dev &d, long long i) {
+template <int S>
+__device__ __forceinline__ double excess(const Dev &d, long long i, uint8_t mk);
+
+// interface neighbours of converted cells receive excess mass.  The
+// converted cell's share e(x) / k(x) is computed here, once, and kept in its
+// mass entry (a converted cell is liquid or gas now, so the entry is not read
+// as a mass again before the cell next becomes interface, which sets it); a
+// cell without interface neighbours keeps its mass for the lost-mass ledger
+template <int S>
+__device__ __forceinline__ void claim_receivers(const Dev &d, long long i, uint8_t mk) {
     int x, y, z;
     coords(d, i, x, y, z);
-    // classes requested at once (this kernel changes marks only)
+    // classes requested at once (this kernel changes marks and the converted
+    // cell's own mass entry only)
     unsigned im = 0;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
         if (yi >= 0 && clsv(d, yi) == CL_I) im |= 1u << q;
     }
-#pragma unroll 1
-    for (int q = 1; q < Q; ++q) {
-        if (!(im & (1u << q))) continue;
-        long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-        uint8_t old = mark_or(d, yi, MK_RECV);
-        if (!(old & MK_RECV)) {
-            uint32_t pos = atomicAdd(&d.cnt[WL_RECV], 1u);
-            if (pos < d.cap) d.list[WL_RECV][pos] = (uint32_t)yi;
-            else atomicOr(d.status, ST_OVERFLOW);
-        }
-    }
+    const int k = __popc(im);
+    if (k > 0) d.m[i] = excess<S>(d, i, mk) / k;
+    mark_append(d, x, y, z, im, MK_RECV, WL_RECV);
 }
 
+template <int S>
 __device__ __forceinline__ void conv_claim_body(const Dev &d, const VB &vb) {
     {
-        LIST_LOOP(WL_FILLED, a) claim_receivers(d, d.list[WL_FILLED][it_a]);
+        LIST_LOOP(WL_FILLED, a) claim_receivers<S>(d, d.list[WL_FILLED][it_a], MK_FILLED);
     }
     {
         LIST_LOOP(WL_EMPTIED, b) {
             long long i = d.list[WL_EMPTIED][it_b];
-            if (d.cmark[i] & MK_EMPTIED) claim_receivers(d, i);
+            const uint8_t mk = d.cmark[i];
+            if (mk & MK_EMPTIED) claim_receivers<S>(d, i, mk);
         }
     }
 }
-__global__ void k_conv_claim(const __grid_constant__ Dev d) { conv_claim_body(d, vb_own()); }
+template <int S>
+__global__ void k_conv_claim(const __grid_constant__ Dev d) { conv_claim_body<S>(d, vb_own()); }
 
 // k(x): interface neighbours of a converted cell (classes after conversion)
 __device__ __forceinline__ int iface_neighbours(const Dev &d, long long i) {
@@ -2113,21 +2120,21 @@ __device__ __forceinline__ void conv_excess_body(const Dev &d, const VB &vb) {
         long long i = d.list[WL_RECV][it_a];
         int x, y, z;
         coords(d, i, x, y, z);
-        double acc = 0.0;
-        // the neighbours' marks requested at once, then the converted ones in q order
-        uint8_t mks[Q];
+        // the neighbours' marks, then the converted ones' shares e(y) / k(y)
+        // (computed when the receivers were claimed), summed in q order
+        unsigned cm = 0;
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
             long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            mks[q] = yi < 0 ? (uint8_t)0 : d.cmark[yi];
+            if (yi >= 0 && (d.cmark[yi] & (MK_FILLED | MK_EMPTIED))) cm |= 1u << q;
         }
-#pragma unroll 1
-        for (int q = 1; q < Q; ++q) {
-            const uint8_t mk = mks[q];
-            if (!(mk & (MK_FILLED | MK_EMPTIED))) continue;
-            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-            acc += excess<S>(d, yi, mk) / iface_neighbours(d, yi);
-        }
+        double sh[Q];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) sh[q] = (cm & (1u << q)) ? d.m[nbr(d, x, y, z, cx(q), cy(q), cz(q))] : 0.0;
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if (cm & (1u << q)) acc += sh[q];
         double m = d.m[i] + acc;
         d.m[i] = m;
         d.phidst[i] = m / cell_density<S>(d, d.fdst, i);
@@ -2571,7 +2578,7 @@ LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkConvInit, LIST_THREADS, 1, conv_init_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFlags, LIST_THREADS, 1, conv_flags_body(d, vb))
-LBMFS_BATCH_BODY(BkConvClaim, LIST_THREADS, 1, conv_claim_body(d, vb))
+template <int S> LBMFS_BATCH_BODY(BkConvClaim, LIST_THREADS, 1, conv_claim_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkConvExcess, LIST_THREADS, 1, conv_excess_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkConvFinish, LIST_THREADS, 1, conv_finish_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkBodies, 32, 1, bodies_body(d, vb))
@@ -2656,7 +2663,7 @@ template <int S> struct Launch {
         mark();
         k_conv_flags<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
-        k_conv_claim<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
+        k_conv_claim<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
         k_conv_excess<S><<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
@@ -2701,7 +2708,7 @@ template <int S> struct BatchStep {
         mark();
         batch_launch<BkConvFlags>(b, SH_LIST, LIST_THREADS, st);
         mark();
-        batch_launch<BkConvClaim>(b, SH_LIST, LIST_THREADS, st);
+        batch_launch<BkConvClaim<S>>(b, SH_LIST, LIST_THREADS, st);
         mark();
         batch_launch<BkConvExcess<S>>(b, SH_LIST, LIST_THREADS, st);
         mark();
