@@ -1990,39 +1990,51 @@ __global__ void k_conv_emptied(const __grid_constant__ Dev d) { conv_emptied_bod
 template <int S>
 __device__ __forceinline__ void conv_init_body(const Dev &d, const VB &vb) {
     {
-        LIST_LOOP(WL_NEWG, a) {
-            long long i = d.list[WL_NEWG][it_a];
+        // one warp per new cell: lane q reads neighbour q (all neighbours'
+        // populations in flight together), the sums are taken in q order
+        // from the gathered values, lane q evaluates f_eq,q
+        const int lane = threadIdx.x & 31;
+        const unsigned wpb = blockDim.x >> 5;
+        const uint32_t n = wl_count(d, WL_NEWG);
+        for (uint32_t w = vb.x * wpb + (threadIdx.x >> 5); w < n; w += vb.nx * wpb) {
+            const long long i = d.list[WL_NEWG][w];
             int x, y, z;
             coords(d, i, x, y, z);
-            if (z > *d.ztop_wr + ZTOP_MARGIN) atomicOr(d.status, ST_TOP);
+            if (lane == 0 && z > *d.ztop_wr + ZTOP_MARGIN) atomicOr(d.status, ST_TOP);
+            double r = 0.0, u[3] = {0.0, 0.0, 0.0};
+            int fluid = 0;
+            if (lane >= 1 && lane < Q) {
+                const long long zi = nbr(d, x, y, z, cx(lane), cy(lane), cz(lane));
+                const int zc = cls(d, zi);
+                if (zc == CL_L || zc == CL_I) {
+                    fluid = 1;
+                    r = cell_rho_u<S>(d, d.fdst, zi, u);
+                }
+            }
             double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
             int cnt = 0;
-            // classes requested at once, then the fluid neighbours in q order
-            unsigned fm = 0;
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const int zc = cls(d, nbr(d, x, y, z, cx(q), cy(q), cz(q)));
-                if (zc == CL_L || zc == CL_I) fm |= 1u << q;
-            }
-#pragma unroll 1
-            for (int q = 1; q < Q; ++q) {
-                if (!(fm & (1u << q))) continue;
-                long long zi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                double u[3];
-                double r = cell_rho_u<S>(d, d.fdst, zi, u);
-                sr += r;
-                su[0] += u[0];
-                su[1] += u[1];
-                su[2] += u[2];
+                const int fq = __shfl_sync(0xffffffffu, fluid, q);
+                const double rq = __shfl_sync(0xffffffffu, r, q), u0 = __shfl_sync(0xffffffffu, u[0], q),
+                             u1 = __shfl_sync(0xffffffffu, u[1], q), u2 = __shfl_sync(0xffffffffu, u[2], q);
+                if (!fq) continue;
+                sr += rq;
+                su[0] += u0;
+                su[1] += u1;
+                su[2] += u2;
                 cnt++;
             }
-            double rm = sr / cnt;
-            double um[3] = {su[0] / cnt, su[1] / cnt, su[2] / cnt};
+            const double rm = sr / cnt;
+            const double um[3] = {su[0] / cnt, su[1] / cnt, su[2] / cnt};
+            const double fl = feq_d(lane < Q ? lane : 0, rm, um);
             double f[Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = feq_d(q, rm, um);
-            Sto<S>::st_cell(d.fdst, i, d.N, f);
-            d.m[i] = 0.0;
+            for (int q = 0; q < Q; ++q) f[q] = __shfl_sync(0xffffffffu, fl, q);
+            if (lane == 0) {
+                Sto<S>::st_cell(d.fdst, i, d.N, f);
+                d.m[i] = 0.0;
+            }
         }
     }
     {
