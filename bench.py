@@ -428,7 +428,7 @@ def main():
     }
     if batch is not None:
         line["batch"] = {
-            "workload": "64 tanks of edge 48..112 (seeded), heeled boxes, FP16-shifted storage, one launch per "
+            "workload": "%d tanks of edge 48..112 (seeded), heeled boxes, FP16-shifted storage, one launch per " % batch["tanks"] +
                         "kernel for all tanks", "dtype": DTYPE["f16s"], "cells": batch["cells"],
             "mlups": batch["mlups"], "ms_per_step": batch["ms_per_step"], "launches": batch["launches"],
             "roofline": {"bound": "hbm", "kernel": "batched k_liquid", "achieved": batch["liquid_gbs"], "peak": hbm,
