@@ -823,7 +823,7 @@ __global__ void k_nb_update(const __grid_constant__ Dev d) { nb_update_body(d, v
 // rounded to nearest (ties away from zero), built from the float's bits with
 // integer operations (no double arithmetic; integer sums are exact, so the
 // block and body totals do not depend on the order of the cells).
-// |v| >= 2^(38 - s) saturates.
+// |v| >= 2^(62 - s) (and a non-finite v) saturates at 2^62 in magnitude.
 constexpr int FX_FORCE = 32, FX_TORQUE = 30;
 __device__ __forceinline__ long long fixed_point(float v, int s) {
     const unsigned b = __float_as_uint(v);
