@@ -64,6 +64,11 @@ enum {
                         rest population that makes the stored cell sum equal the
                         collision density; arithmetic in float */
 };
+/* With every storage the interface mass and fill levels, the mass ledger and
+ * the rigid-body state stay in double.  The float storages sum the momentum
+ * exchange per cell in float and across cells exactly: the uniform
+ * gas-pressure part as 64-bit integers, the rest in fixed point (2^-32 force,
+ * 2^-30 torque), converted to double per body. */
 
 /* cell classes (init_flags input and LBM_FS_FIELD_FLAGS output) */
 enum { LBM_FS_LIQUID = 1, LBM_FS_INTERFACE = 2, LBM_FS_GAS = 4, LBM_FS_OBSTACLE = 8 };
