@@ -39,14 +39,40 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments, trailing blanks and empty lines
+    (string and character literals are kept as they are)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            while i < n and src[i] != "\n":
+                i += 1
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_source_hash() -> str:
-    """sha256 of the kernel sources, to tie a stored ncu capture to the code."""
+    """sha256 of the kernel sources without their comments, to tie a stored
+    ncu capture to the code."""
     import hashlib
 
     h = hashlib.sha256()
     for f in ("lbmfs_kernels.cuh", "lbmfs_internal.h"):
-        with open(os.path.join(ROOT, "paper_1201_0351_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1201_0351_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode("utf-8"))
     return h.hexdigest()
 
 
