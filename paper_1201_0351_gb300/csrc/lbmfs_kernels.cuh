@@ -818,7 +818,9 @@ __device__ __forceinline__ void nb_update_body(const Dev &d, const VB &vb) {
 }
 __global__ void k_nb_update(const __grid_constant__ Dev d) { nb_update_body(d, vb_own()); }
 
-// ---- C4: momentum exchange at the links into body vb.y (state at t)
+// ---- C4: momentum exchange at the links into body vb.y (state at t):
+// Sec. 2.3 Eqs. momentumexchange, netforce, torque; Sec. 2.4 Eq.
+// momentuminterface for interface cells
 // Fixed-point sums of the float storages' per-cell force remainders: v * 2^s
 // rounded to nearest (ties away from zero), built from the float's bits with
 // integer operations (no double arithmetic; integer sums are exact, so the
@@ -1187,14 +1189,13 @@ __device__ __noinline__ Bounce<typename Sto<S>::R> bounce_back(const Dev &d, int
     }
 }
 
-// ---- C1 + C2 for liquid cells; interface cells are listed for k_interface
+// ---- C1 + C2 for liquid cells (Sec. 2.1 Eqs. stream, lbgk, forceterm;
+// Sec. 2.3 Eq. noslip); interface cells are listed for k_interface
 template <int S>
 __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int y, int z0, int z1);
 
-// one block: a row segment of BULK_THREADS cells at (y, z) for LBMFS_BULK_ZB
-// consecutive z (amortises the launch of blocks that meet only gas)
 // A block covers BULK_THREADS consecutive cells of an xy-plane (row ends
 // wrap to the next row, so narrow grids keep every lane busy) for zb
 // consecutive z: grid (ceil(nx ny / BULK_THREADS), 1, ceil(nz / zb)).
@@ -2187,6 +2188,8 @@ template <int S>
 __global__ void k_conv_finish(const __grid_constant__ Dev d) { conv_finish_body<S>(d, vb_own()); }
 
 // ----------------------------------------------- C5: rigid-body update
+// (the role the paper gives the pe engine, Sec. 2.3: the body moves under the
+// hydrodynamic force and torque and gravity; the integrator is this build's)
 
 // one warp per body: fixed-order sum of the force partials, then the update
 __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *acc);
