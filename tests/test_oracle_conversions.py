@@ -60,6 +60,17 @@ def test_filled_cell_converts_and_gas_neighbours_join_interface():
     m = s.fields()["mass"].reshape(n, n, n)
     new = [m[4, 3 + dy, 3 + dx] for dx, dy, dz in NEIGH if dz == 1]
     assert np.ptp(new) == 0.0 and new[0] > 0.03
+    # at rest every link's mass exchange vanishes (f = w on both sides), so the
+    # filled cell keeps m = 1.6 at rho = 1: its excess e = 0.6 goes in equal
+    # shares to its k = 13 interface neighbours after the conversion (the 8 of
+    # its own layer and the 5 new ones); other interface cells keep m = 0.5
+    e = 1.6 - 1.0
+    for dx, dy, dz in NEIGH:
+        if dz == 1:
+            assert abs(m[4, 3 + dy, 3 + dx] - e / 13) <= 1e-14
+        elif dz == 0:
+            assert abs(m[3, 3 + dy, 3 + dx] - (0.5 + e / 13)) <= 1e-14
+    assert abs(m[3, 0, 0] - 0.5) <= 1e-14 and abs(m[3, 6, 6] - 0.5) <= 1e-14
     assert _ledger_ok(s)
 
 
