@@ -92,6 +92,16 @@ def test_emptied_cell_converts_and_liquid_neighbours_join_interface():
     for dx, dy, dz in NEIGH:
         if dz == -1:
             assert 0.9 < fl[2, 3 + dy, 3 + dx] < 1.0  # phi = 1 plus a share of the negative excess
+    # at rest the emptied cell keeps m = -0.5 (its excess); the new interface
+    # cells start at m = rho = 1, and each of the k = 13 interface neighbours
+    # after the conversion (8 of its layer, 5 new) gains e / 13
+    m = f["mass"].reshape(n, n, n)
+    e = -0.5
+    for dx, dy, dz in NEIGH:
+        if dz == -1:
+            assert abs(m[2, 3 + dy, 3 + dx] - (1.0 + e / 13)) <= 1e-14
+        elif dz == 0:
+            assert abs(m[3, 3 + dy, 3 + dx] - (0.5 + e / 13)) <= 1e-14
     assert _ledger_ok(s)
 
 
