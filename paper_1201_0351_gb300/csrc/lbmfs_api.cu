@@ -45,10 +45,14 @@ lbm_fs_status check_handle(lbm_fs *h) {
 
 lbm_fs_status read_status(lbm_fs *h) {
     uint32_t st = 0;
+    CK(cudaMemcpyAsync(&st, h->d[0].status, sizeof st, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    CK(cudaMemcpy(&st, h->d[0].status, sizeof st, cudaMemcpyDeviceToHost));
+    return status_bits(st);
+}
+
+lbm_fs_status status_bits(uint32_t st) {
     if (st & ST_OVERFLOW) return fail(LBM_FS_EOVERFLOW, "a device worklist overflowed%s");
-    if (st & ST_TIMEOUT) return fail(LBM_FS_ETIMEOUT, "a bounded wait for staged rows gave up%s");
+    if (st & ST_TIMEOUT) return fail(LBM_FS_ETIMEOUT, "a bounded device wait (staged rows) gave up%s");
     if (st & ST_NONFINITE) return fail(LBM_FS_EUNSTABLE, "non-finite or non-positive density in a fluid cell%s");
     if (st & ST_LIQUID_GAS) return fail(LBM_FS_EUNSTABLE, "a liquid cell touched a gas cell (open interface layer)%s");
     if (st & ST_CONTACT) return fail(LBM_FS_EUNSTABLE, "a moving body reached a domain wall (body-wall contact is not modelled)%s");
@@ -392,7 +396,9 @@ lbm_fs_status lbm_fs_body_states(lbm_fs *h, int32_t first, int32_t count, lbm_fs
         return fail(LBM_FS_EINVAL, "bad body range%s");
     if (count == 0) return read_status(h);
     std::vector<Body> hb(count);
+    uint32_t st = 0;  // the status word comes with the bodies: one synchronisation
     CK(cudaMemcpyAsync(hb.data(), h->d[0].bodies + first, sizeof(Body) * count, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&st, h->d[0].status, sizeof st, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     for (int32_t b = 0; b < count; ++b) {
         for (int k = 0; k < 3; ++k) {
@@ -405,7 +411,7 @@ lbm_fs_status lbm_fs_body_states(lbm_fs *h, int32_t first, int32_t count, lbm_fs
         for (int k = 0; k < 4; ++k) out[b].quat[k] = hb[b].q[k];
         out[b].S = hb[b].S;
     }
-    return read_status(h);
+    return status_bits(st);
 }
 
 lbm_fs_status lbm_fs_forces(lbm_fs *h, int32_t id, double F[3], double T[3], double center[3], double quat[4]) {

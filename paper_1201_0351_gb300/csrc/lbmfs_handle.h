@@ -57,6 +57,8 @@ lbm_fs_status cuda_fail(cudaError_t e, const char *where);
 lbm_fs_status check_handle(lbm_fs *h);
 // synchronise the handle's stream and map its sticky device bits to a status
 lbm_fs_status read_status(lbm_fs *h);
+// map a copy of the device status word to a status (first sticky bit wins)
+lbm_fs_status status_bits(uint32_t st);
 // before the first step: book the initial liquid mass (enqueued on h->st)
 void begin_mass(lbm_fs *h);
 }  // namespace lbmfs
