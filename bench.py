@@ -305,13 +305,24 @@ class _Null:
 
 def e2e_run(sc, storage, steps):
     """Through the public API with host buffers: create (uploads the initial
-    host arrays), then every step lbm_fs_step + lbm_fs_body_states of all
+    state from pinned host arrays), then every step lbm_fs_step + lbm_fs_body_states of all
     bodies (device -> host read of the step's forces, torques and poses, as a
     host-side rigid-body coupling would do), timed on the host clock."""
+    import dataclasses
+
     import torch
 
     from paper_1201_0351_gb300 import lbm_fs
 
+    # the job's inputs (the initial state) wait in pinned host memory, filled
+    # before the timed region; their host-to-device copy is timed
+    pinned = {}
+    for key in ("flags", "fill", "rho"):
+        a = np.ascontiguousarray(getattr(sc, key))
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:1].copy()).dtype, pin_memory=True)
+        t.numpy()[...] = a
+        pinned[key] = t.numpy()
+    sc = dataclasses.replace(sc, **pinned)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim = lbm_fs.Simulation(sc, storage=storage, use_graphs=True, host_init=True)
@@ -327,7 +338,7 @@ def e2e_run(sc, storage, steps):
     d2h = sim.nbodies * C_BODY_BYTES
     return dict(value=n * steps / (t1 - t0) / 1e6, unit="MLUPS", h2d_bytes_per_step=h2d // steps,
                 d2h_bytes_per_step=d2h, steps=steps,
-                covers="create from host arrays, then every step lbm_fs_step + lbm_fs_body_states")
+                covers="create from pinned host arrays, then every step lbm_fs_step + lbm_fs_body_states")
 
 
 def cpu_baseline(sc_full, target_s=15.0):
