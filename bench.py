@@ -271,22 +271,24 @@ def run_batch(scenes, storage, steps, warmup, kernel_steps, separate_steps=20, b
     liquid_bytes = n_liq * b_fluid + (n_liq + n_if) * 1
     liquid_ms = kt["liquid"] / kernel_steps
     # the same tanks as separate handles (each with its own captured graphs)
-    sims = [lbm_fs.Simulation(sc, storage=storage) for sc in scenes]
-    for sim in sims:
-        sim.step(2)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    start.record(stream)
-    for _ in range(separate_steps):
+    ms_sep = None
+    if separate_steps > 0:
+        sims = [lbm_fs.Simulation(sc, storage=storage) for sc in scenes]
         for sim in sims:
-            sim.step(1)
-    end.record(stream)
-    end.synchronize()
-    ms_sep = start.elapsed_time(end) / separate_steps
-    for sim in sims:
-        sim.close()
-    del sims
-    torch.cuda.empty_cache()
+            sim.step(2)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        start.record(stream)
+        for _ in range(separate_steps):
+            for sim in sims:
+                sim.step(1)
+        end.record(stream)
+        end.synchronize()
+        ms_sep = start.elapsed_time(end) / separate_steps
+        for sim in sims:
+            sim.close()
+        del sims
+        torch.cuda.empty_cache()
     total_k = sum(kt.values())
     return dict(storage=storage, tanks=len(scenes), cells=cells, ms_total=ms, ms_per_step=ms / steps,
                 mlups=cells * steps / (ms * 1e-3) / 1e6, step_gbs=step_bytes / (ms / steps * 1e-3) / 1e9,
@@ -443,6 +445,9 @@ def main():
 
         batch = run_batch(inputs.batched_sweep_tanks(args.batch_tanks), "f16s", args.steps, max(args.warmup, 3), 5,
                           barrier=barrier)
+        # the FP32-stored batched form on the same tanks (no separate-handle comparison)
+        batch32 = run_batch(inputs.batched_sweep_tanks(args.batch_tanks), "f32", args.steps, max(args.warmup, 3), 5,
+                            separate_steps=0, barrier=barrier)
     n = sc.nx * sc.ny * sc.nz
     ms, value = whole_job(main_run["ms_total"], n, args.steps, ws, "cuda")
     e2e = e2e_run(sc, "f32", args.e2e_steps or sc.steps)
@@ -477,7 +482,13 @@ def main():
                          "algorithmic_bytes_per_launch": batch["liquid_bytes"],
                          "step_achieved_gbs": batch["step_gbs"], "step_frac": batch["step_gbs"] / hbm},
             "kernel_share": batch["kernel_share"], "autotune": batch["autotune"],
-            "separate_handles_ms_per_step": batch["separate_ms_per_step"]}
+            "separate_handles_ms_per_step": batch["separate_ms_per_step"],
+            "f32": {"dtype": DTYPE["f32"], "mlups": batch32["mlups"], "ms_per_step": batch32["ms_per_step"],
+                    "launches": batch32["launches"], "autotune": batch32["autotune"],
+                    "roofline": {"bound": "hbm", "kernel": "batched k_liquid", "achieved": batch32["liquid_gbs"],
+                                 "peak": hbm, "unit": "GB/s", "frac": batch32["liquid_gbs"] / hbm,
+                                 "algorithmic_bytes_per_launch": batch32["liquid_bytes"],
+                                 "step_achieved_gbs": batch32["step_gbs"], "step_frac": batch32["step_gbs"] / hbm}}}
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
