@@ -155,8 +155,9 @@ typedef struct {
                               - lost_excess + wall_source (to rounding) */
 } lbm_fs_stats_t;
 
-/* field selectors for lbm_fs_read_fields / lbm_fs_write_fields; dst[k] is the
- * buffer for bit k.  Layouts: FLAGS uint8[N]; FILL, MASS, RHO double[N];
+/* field selectors for lbm_fs_read_fields; dst[k] is the buffer for bit k.
+ * (The state is set only at creation, from init_flags / init_fill / init_rho /
+ * init_vel: there is no write-back call.)  Layouts: FLAGS uint8[N]; FILL, MASS, RHO double[N];
  * VEL double[3N] (xyz per cell); F double[19N] (SoA, [q][idx]).  FILL is 1 for
  * liquid, phi for interface, 0 else; MASS is rho / m / 0; RHO and VEL are the
  * density and the velocity of the last collision (sum c f / rho - a) of liquid
