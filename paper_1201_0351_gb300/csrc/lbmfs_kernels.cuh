@@ -79,7 +79,7 @@ constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2
 #define LBMFS_FORCE_ROWS 1  // range rows per warp in the float-storage force kernel
 #endif
 #ifndef LBMFS_IFACE_MINB
-#define LBMFS_IFACE_MINB 5  // resident blocks per SM asked of ptxas for the interface kernel (102 registers)
+#define LBMFS_IFACE_MINB 6  // resident blocks per SM asked of ptxas for the interface kernel (80 registers)
 #endif
 #ifndef LBMFS_IFACE_GRID
 #define LBMFS_IFACE_GRID (16 * 152)  // blocks of the single-tank interface kernel (16 per SM)
