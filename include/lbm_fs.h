@@ -119,7 +119,37 @@ typedef struct {
      * its lowest axis); all zero: resting walls.  The mass a moving wall adds
      * to liquid cells is booked in lbm_fs_stats_t.wall_source. */
     double wall_vel[6][3];
+    /* Readings of the paper where it is silent.  A field below is used only
+     * when its LBM_FS_READING_* bit is set in `readings`; otherwise its default
+     * applies (a zeroed struct gets every default).
+     *  normal_deadband (default 1e-3, >= 0): Eq. reconstruct rebuilds the
+     *    populations of the directions with c_q . n <= 0 (Sec. 2.2); a
+     *    direction counts when c_q . n < -normal_deadband.  0 is the bare
+     *    sign test, under which the noise of the estimated normal decides the
+     *    tangential directions of a flat surface and the spurious interface
+     *    velocities exceed the 1e-5 that Sec. 3.2.1 reports;
+     *  virtual_mass (default 1, >= 0): coefficient C of the rigid-body update
+     *    (m + C m_f) dv_{n+1} = F + m g + C m_f dv_n (the paper hands the
+     *    bodies to an external engine, Sec. 2.3); 0 is the explicit update;
+     *  force_mean (default 1): the update is driven by (F_n + F_{n-1}) / 2
+     *    (F_n on the first step); 0: by F_n (Eq. netforce / torque);
+     *  neighbour_rule (default 1): besides the fill thresholds of Sec. 2.2,
+     *    an interface cell with gas but no liquid among its 18 neighbours
+     *    empties and one with liquid but no gas fills; 0: thresholds only. */
+    uint32_t readings;
+    double normal_deadband;
+    double virtual_mass;
+    int32_t force_mean;
+    int32_t neighbour_rule;
 } lbm_fs_params;
+
+/* bits of lbm_fs_params.readings */
+enum {
+    LBM_FS_READING_DEADBAND = 1u << 0,
+    LBM_FS_READING_VIRTUAL_MASS = 1u << 1,
+    LBM_FS_READING_FORCE_MEAN = 1u << 2,
+    LBM_FS_READING_NEIGHBOUR_RULE = 1u << 3
+};
 
 typedef struct {
     double center[3];      /* centre of mass (world) */
@@ -186,11 +216,29 @@ lbm_fs_status lbm_fs_destroy(lbm_fs *h);
 lbm_fs_status lbm_fs_add_box(lbm_fs *h, const lbm_fs_box *b, int32_t *out_id);
 
 /* Enqueues nsteps time steps on the handle's stream and returns without
- * waiting. */
+ * waiting.  One step, in order: the momentum-exchange force and torque on
+ * every body from the state at t (Sec. 2.3 Eqs. momentumexchange, netforce,
+ * torque; Sec. 2.4 Eq. momentuminterface); stream with no-slip and moving-wall
+ * bounce-back (Sec. 2.1 Eq. stream, Sec. 2.3 Eq. noslip), the atmosphere
+ * reconstruction and the interface mass exchange (Sec. 2.2 Eq. reconstruct and
+ * the mass balance that follows it); BGK collision with the gravity force term
+ * (Sec. 2.1 Eqs. lbgk, equilibrium, forceterm, density, momentum) and the new
+ * fill levels; the interface conversions with excess-mass redistribution
+ * (Sec. 2.2, last paragraph); the rigid-body update (Sec. 2.3); the obstacle
+ * remapping, cells covered and uncovered by the moved bodies with the
+ * obstacle-to-fluid rule (Sec. 2.3 body discretisation, Sec. 2.4).
+ * nsteps < 0 gives LBM_FS_EINVAL; 0 enqueues nothing.  Device-side failures
+ * surface at the next synchronising call (header comment). */
 lbm_fs_status lbm_fs_step(lbm_fs *h, int32_t nsteps);
 
-/* Synchronises and returns the force and torque of the last step on body id
- * and its current pose.  Any pointer may be NULL. */
+/* Synchronises and returns the force F and torque T of the last step on body
+ * id (Sec. 2.3 Eqs. netforce and torque: the momentum exchange of Eq.
+ * momentumexchange summed over the body's links, with Eq. momentuminterface
+ * on interface and gas cells; torque about the body's centre with the lever
+ * arm from the fluid cell's centre; FP64) and its current pose (centre,
+ * quaternion (w, x, y, z) body -> world).  Caller-owned host arrays; any
+ * pointer may be NULL.  An unknown id gives LBM_FS_EINVAL; before the first
+ * step F and T are zero. */
 lbm_fs_status lbm_fs_forces(lbm_fs *h, int32_t id, double F[3], double T[3],
                             double center[3], double quat[4]);
 lbm_fs_status lbm_fs_body_state(lbm_fs *h, int32_t id, lbm_fs_body_state_t *out);
@@ -200,7 +248,12 @@ lbm_fs_status lbm_fs_body_state(lbm_fs *h, int32_t id, lbm_fs_body_state_t *out)
 lbm_fs_status lbm_fs_body_states(lbm_fs *h, int32_t first, int32_t count, lbm_fs_body_state_t *out);
 
 /* Synchronises and copies the selected fields into caller-owned buffers (host
- * or device, per dst_on_device), each sized as documented above. */
+ * or device, per dst_on_device), each sized as documented above: the cell
+ * classes, the fill level phi = m / rho of Sec. 2.2, the mass, and the
+ * density and velocity of Sec. 2.1 Eqs. density and momentum (of the last
+ * collision: rho = sum f*, u = sum c f* / rho - a), and the populations.
+ * dst[k] serves bit k of mask; unselected entries may be NULL, a selected
+ * NULL gives LBM_FS_EINVAL. */
 lbm_fs_status lbm_fs_read_fields(lbm_fs *h, uint32_t mask, void *const *dst,
                                  int32_t dst_on_device);
 

@@ -22,8 +22,12 @@
  * Eq. forceterm are garbled), the cell's own density in the moving-wall term,
  * u_w at the link midpoint, the anti-bounce-back of the cell's own outgoing
  * population in Eq. reconstruct, a central-difference normal with
- * c.n < -1e-3 (a dead band against noise), eps = 1e-2, Jacobi-style conversions with equal excess-mass split,
- * and the obstacle-to-fluid priority interface > liquid > gas.
+ * c.n < -deadband (default 1e-3, a dead band against noise; 0 gives the bare
+ * sign test), eps = 1e-2, Jacobi-style conversions with equal excess-mass
+ * split, and the obstacle-to-fluid priority interface > liquid > gas.  The
+ * readings that are options (dead band, the neighbour conversion rule, the
+ * virtual-mass coefficient and the two-step force mean of the rigid-body
+ * update) are set per simulation with orc_set_readings().
  *
  * Floating-point expression order is written out explicitly (left to right,
  * q in the order C,W,E,N,S,T,B,TW,TE,TN,TS,NW,NE,SW,SE,BW,BE,BN,BS of the
@@ -42,10 +46,11 @@ enum { M_FIXED = 0, M_FREE = 1, M_ROT_AXIS = 2, M_DAMP = 0x100 };
 /* Eq. reconstruct selects the directions with c_q . n <= 0.  A direction
  * tangential to a flat surface has c_q . n = 0 up to noise (rounding, storage
  * precision), and a bare sign test turns that noise into a discontinuous
- * reconstruct / stream decision; directions count as pointing out of the gas
- * only when c_q . n < -1e-3, i.e. when the fill level changes by more than
- * 2e-3 across the cell. */
-#define NORMAL_DEADBAND 1e-3
+ * reconstruct / stream decision; by default directions count as pointing out
+ * of the gas only when c_q . n < -1e-3, i.e. when the fill level changes by
+ * more than 2e-3 across the cell (orc_set_readings changes it; 0 is the
+ * strict sign test c_q . n < 0). */
+#define DEFAULT_DEADBAND 1e-3
 
 /* D3Q19 velocities in the order of the paper's stencil figure. */
 static const int C[Q][3] = {
@@ -81,9 +86,9 @@ typedef struct {
     int shape;           /* 0: box of half extents h; 1: sphere of radius h[0] */
 } body_t;
 
-/* virtual-mass coefficient of the rigid-body update (Schwarz, Kempe and
- * Froehlich, J. Comput. Phys. 281 (2015)) */
-#define VIRTUAL_MASS 1.0
+/* default virtual-mass coefficient of the rigid-body update (Schwarz, Kempe
+ * and Froehlich, J. Comput. Phys. 281 (2015)) */
+#define DEFAULT_VIRTUAL_MASS 1.0
 
 struct orc_sim {
     int nx, ny, nz;
@@ -104,6 +109,11 @@ struct orc_sim {
     int have_m0, err;
     long t;
     long counts[6];
+    /* readings (orc_set_readings) */
+    double deadband;     /* Eq. reconstruct: c.n < -deadband selects a direction */
+    double vmass;        /* virtual-mass coefficient C of the rigid-body update */
+    int force_mean;      /* 1: the update is driven by (F_n + F_{n-1}) / 2; 0: by F_n */
+    int nb_rule;         /* 1: interface cells without liquid (gas) neighbours empty (fill) */
 };
 
 /* ---------------------------------------------------------------- helpers */
@@ -323,6 +333,10 @@ orc_sim *orc_create(int nx, int ny, int nz, unsigned periodic, double tau, const
     }
     s->rho_g = rho_gas;
     s->eps = eps;
+    s->deadband = DEFAULT_DEADBAND;
+    s->vmass = DEFAULT_VIRTUAL_MASS;
+    s->force_mean = 1;
+    s->nb_rule = 1;
     s->flag = (uint8_t *)calloc(s->n, 1);
     s->body = (int *)calloc(s->n, sizeof(int));
     s->f = (double *)calloc(s->n * Q, sizeof(double));
@@ -520,7 +534,7 @@ static void stream_collide(orc_sim *s) {
                 if (cl == IFC) {
                     for (int q = 1; q < Q; ++q) {
                         double cn = (C[q][0] * n[0] + C[q][1] * n[1]) + C[q][2] * n[2];
-                        if (cn < -NORMAL_DEADBAND && scl[q] != OBS && scl[q] != WALL) {
+                        if (cn < -s->deadband && scl[q] != OBS && scl[q] != WALL) {
                             int qb = OPP[q];
                             fp[q] = (feq(q, rg, ux) + feq(qb, rg, ux)) - fo[qb];
                         }
@@ -583,7 +597,7 @@ static void conversions(orc_sim *s) {
             mark[i] |= CV_FILLED;
         } else if (s->phin[i] <= -s->eps) {
             mark[i] |= CV_EMPTIED;
-        } else if (g_mutation != 9) {
+        } else if (s->nb_rule && g_mutation != 9) {
             int x = (int)(i % s->nx), y = (int)((i / s->nx) % s->ny), z = (int)(i / ((long)s->nx * s->ny));
             int liq = 0, gas = 0;
             for (int q = 1; q < Q; ++q) {
@@ -703,21 +717,33 @@ static void conversions(orc_sim *s) {
 
 /* ------------------------------------------------------------------ C5 */
 
-/* Rigid-body update replacing the external physics engine.  An explicit
- * update of a body that is light compared with the liquid is unstable with the
- * momentum-exchange force (the bounce-back answers a velocity change within
- * one step: the added-mass instability), so the update uses the virtual-mass
- * scheme: (m + C m_f) dv_{n+1} = Fh_n + m g + C m_f dv_n, with m_f the mass of
- * liquid of the body's volume and dv the per-step velocity increment; the
- * same for the angular velocity in the body frame.  Fh_n (and the torque
- * likewise) is the mean of the momentum-exchange force of this step and the
- * previous one (the force itself on the first step): near tau = 1/2 the BGK
- * modes that flip sign every step are barely damped, and a force that flips
- * with them feeds back through the wall velocity into a growing oscillation
- * of the body and the liquid under it; the two-step mean removes that
- * component and leaves slower forcing unchanged.  Position: semi-implicit
- * Euler; orientation: first-order quaternion update and renormalisation. */
+/* Rigid-body update replacing the external physics engine (Sec. 2.3 leaves
+ * it to pe).  An explicit update of a body that is light compared with the
+ * liquid is unstable with the momentum-exchange force (the bounce-back
+ * answers a velocity change within one step: the added-mass instability), so
+ * the update uses the virtual-mass scheme:
+ *     (m + C m_f) dv_{n+1} = Fh_n + m g + C m_f dv_n,
+ * m the body's mass, m_f the mass of liquid of its volume (liquid density 1),
+ * dv the per-step velocity increment and C the virtual-mass coefficient
+ * (C = 0 is the explicit Newton update); the same for the angular velocity in
+ * the body frame, with the body's principal moments I, the displaced liquid's
+ * I / rho_s and the gyroscopic term omega x (I omega) of Euler's equations.
+ * Fh_n (and the torque likewise) is the mean of the momentum-exchange force of
+ * this step and the previous one (the force itself on the first step), or the
+ * force of this step alone when the two-step mean is switched off: near
+ * tau = 1/2 the BGK modes that flip sign every step are barely damped, and a
+ * force that flips with them feeds back through the wall velocity into a
+ * growing oscillation of the body and the liquid under it; the mean removes
+ * that component and leaves slower forcing unchanged.  Box of half extents h:
+ * V = 8 h0 h1 h2, I_x = m (h1^2 + h2^2) / 3 (= m (b^2 + c^2) / 12 for the full
+ * edges b = 2 h1, c = 2 h2); sphere: V = 4/3 pi r^3, I = 2/5 m r^2.  With
+ * rotation about one axis a only, the torque is projected on a and the moment
+ * of inertia is a^T I a in the body frame.  Position: semi-implicit Euler
+ * (o += v_{n+1}); orientation: first-order update of the quaternion by the
+ * world-frame angular velocity, q <- normalise(q + 1/2 (0, omega) q), which
+ * turns the body by 2 atan(|omega| / 2) per step. */
 static void bodies_step(orc_sim *s) {
+    const double C = s->vmass;
     for (int bi = 0; bi < s->nb; ++bi) {
         body_t *b = &s->b[bi];
         int base = b->mode & 0xff;
@@ -727,8 +753,9 @@ static void bodies_step(orc_sim *s) {
         }
         double Fh[3], Th[3];
         for (int k = 0; k < 3; ++k) {
-            Fh[k] = b->nF ? 0.5 * (b->F[k] + b->Fp[k]) : b->F[k];
-            Th[k] = b->nF ? 0.5 * (b->T[k] + b->Tp[k]) : b->T[k];
+            int mean = s->force_mean && b->nF;
+            Fh[k] = mean ? 0.5 * (b->F[k] + b->Fp[k]) : b->F[k];
+            Th[k] = mean ? 0.5 * (b->T[k] + b->Tp[k]) : b->T[k];
             b->Fp[k] = b->F[k];
             b->Tp[k] = b->T[k];
         }
@@ -740,15 +767,17 @@ static void bodies_step(orc_sim *s) {
             I[0] = I[1] = I[2] = (0.4 * mass) * (b->h[0] * b->h[0]);
         } else {
             vol = ((8.0 * b->h[0]) * b->h[1]) * b->h[2];
+            if (g_mutation == 14) vol = (b->h[0] * b->h[1]) * b->h[2];
             mass = b->dens * vol;
-            I[0] = (mass / 3.0) * (b->h[1] * b->h[1] + b->h[2] * b->h[2]);
-            I[1] = (mass / 3.0) * (b->h[0] * b->h[0] + b->h[2] * b->h[2]);
-            I[2] = (mass / 3.0) * (b->h[0] * b->h[0] + b->h[1] * b->h[1]);
+            double f = g_mutation == 10 ? 12.0 : 3.0;
+            I[0] = (mass / f) * (b->h[1] * b->h[1] + b->h[2] * b->h[2]);
+            I[1] = (mass / f) * (b->h[0] * b->h[0] + b->h[2] * b->h[2]);
+            I[2] = (mass / f) * (b->h[0] * b->h[0] + b->h[1] * b->h[1]);
         }
         double If[3] = {I[0] / b->dens, I[1] / b->dens, I[2] / b->dens}; /* inertia of the displaced liquid */
-        double den = mass + VIRTUAL_MASS * vol;
+        double den = g_mutation == 11 ? mass : mass + C * vol;
         for (int k = 0; k < 3; ++k) {
-            double num = (Fh[k] + mass * s->grav[k]) + VIRTUAL_MASS * (vol * b->dv[k]);
+            double num = (Fh[k] + mass * s->grav[k]) + C * (vol * b->dv[k]);
             b->dv[k] = num / den;
             b->v[k] = b->v[k] + b->dv[k];
         }
@@ -764,7 +793,7 @@ static void bodies_step(orc_sim *s) {
             double Ia = (ab[0] * ab[0] * I[0] + ab[1] * ab[1] * I[1]) + ab[2] * ab[2] * I[2];
             double Ifa = Ia / b->dens;
             double ws = (b->w[0] * ax[0] + b->w[1] * ax[1]) + b->w[2] * ax[2];
-            b->dw[0] = (ta + VIRTUAL_MASS * (Ifa * b->dw[0])) / (Ia + VIRTUAL_MASS * Ifa);
+            b->dw[0] = (ta + C * (Ifa * b->dw[0])) / (Ia + C * Ifa);
             ws = ws + b->dw[0];
             for (int k = 0; k < 3; ++k) b->w[k] = ws * ax[k];
         } else {
@@ -777,8 +806,10 @@ static void bodies_step(orc_sim *s) {
             gy[0] = wb[1] * L[2] - wb[2] * L[1];
             gy[1] = wb[2] * L[0] - wb[0] * L[2];
             gy[2] = wb[0] * L[1] - wb[1] * L[0];
+            if (g_mutation == 12)
+                for (int k = 0; k < 3; ++k) gy[k] = -gy[k];
             for (int k = 0; k < 3; ++k) {
-                b->dw[k] = ((tb[k] - gy[k]) + VIRTUAL_MASS * (If[k] * b->dw[k])) / (I[k] + VIRTUAL_MASS * If[k]);
+                b->dw[k] = ((tb[k] - gy[k]) + C * (If[k] * b->dw[k])) / (I[k] + C * If[k]);
                 wb[k] = wb[k] + b->dw[k];
             }
             for (int k = 0; k < 3; ++k) b->w[k] = (R[k][0] * wb[0] + R[k][1] * wb[1]) + R[k][2] * wb[2];
@@ -798,6 +829,11 @@ static void bodies_step(orc_sim *s) {
         double dx = qw * w[0] + (w[1] * qz - w[2] * qy);
         double dy = qw * w[1] + (w[2] * qx - w[0] * qz);
         double dz = qw * w[2] + (w[0] * qy - w[1] * qx);
+        if (g_mutation == 13) { /* q (x) (0, omega): the body-frame product */
+            dx = qw * w[0] - (w[1] * qz - w[2] * qy);
+            dy = qw * w[1] - (w[2] * qx - w[0] * qz);
+            dz = qw * w[2] - (w[0] * qy - w[1] * qx);
+        }
         double nq[4] = {qw + 0.5 * dw, qx + 0.5 * dx, qy + 0.5 * dy, qz + 0.5 * dz};
         double norm = sqrt(((nq[0] * nq[0] + nq[1] * nq[1]) + nq[2] * nq[2]) + nq[3] * nq[3]);
         for (int k = 0; k < 4; ++k) b->q[k] = nq[k] / norm;
@@ -993,7 +1029,7 @@ void orc_get_body(const orc_sim *s, int bi, double F[3], double T[3], double *S,
     if (S) *S = b->S;
 }
 
-void orc_get_ledger(const orc_sim *s, double out[5]) {
+void orc_get_ledger(const orc_sim *s, double out[6]) {
     out[0] = s->covered;
     out[1] = s->uncovered;
     out[2] = s->lost;
@@ -1034,4 +1070,23 @@ void orc_set_surface_tension(orc_sim *s, double sigma) { s->sigma = sigma; }
 void orc_set_wall_velocity(orc_sim *s, const double v[18]) {
     for (int f = 0; f < 6; ++f)
         for (int j = 0; j < 3; ++j) s->wall_vel[f][j] = v[3 * f + j];
+}
+
+void orc_set_readings(orc_sim *s, double deadband, double virtual_mass, int force_mean, int neighbour_rule) {
+    s->deadband = deadband;
+    s->vmass = virtual_mass;
+    s->force_mean = force_mean != 0;
+    s->nb_rule = neighbour_rule != 0;
+}
+
+void orc_set_body_force(orc_sim *s, int bi, const double F[3], const double T[3]) {
+    for (int k = 0; k < 3; ++k) {
+        s->b[bi].F[k] = F[k];
+        s->b[bi].T[k] = T[k];
+    }
+}
+
+void orc_bodies_step(orc_sim *s) {
+    init_lattice();
+    bodies_step(s);
 }

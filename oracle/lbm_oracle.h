@@ -75,6 +75,20 @@ void orc_set_surface_tension(orc_sim *s, double sigma);
 /* velocities of the wall faces x-, x+, y-, y+, z-, z+ (3 each; Eq. noslip
  * with u_w at domain walls); zero by default */
 void orc_set_wall_velocity(orc_sim *s, const double v[18]);
+/* readings where the paper is silent (defaults 1e-3, 1, 1, 1):
+ *   deadband       Eq. reconstruct rebuilds a direction when c_q . n < -deadband
+ *                  (0: the strict sign test);
+ *   virtual_mass   C of the rigid-body update (0: explicit Newton update);
+ *   force_mean     1: the update is driven by (F_n + F_{n-1}) / 2, 0: by F_n;
+ *   neighbour_rule 1: an interface cell without liquid neighbours (but with
+ *                  gas ones) empties, one without gas neighbours (but with
+ *                  liquid ones) fills; 0: the fill thresholds only. */
+void orc_set_readings(orc_sim *s, double deadband, double virtual_mass, int force_mean, int neighbour_rule);
+/* C5 alone, for its pins: set the force and torque of body b as if the
+ * momentum exchange had produced them, then run the rigid-body update of every
+ * body (no remapping of cells) */
+void orc_set_body_force(orc_sim *s, int b, const double F[3], const double T[3]);
+void orc_bodies_step(orc_sim *s);
 
 #ifdef __cplusplus
 }

@@ -64,6 +64,9 @@ def _load():
         lib.orc_set_mutation.argtypes = [I]
         lib.orc_set_surface_tension.argtypes = [P, C.c_double]
         lib.orc_set_wall_velocity.argtypes = [P, D]
+        lib.orc_set_readings.argtypes = [P, C.c_double, C.c_double, I, I]
+        lib.orc_set_body_force.argtypes = [P, I, D, D]
+        lib.orc_bodies_step.argtypes = [P]
         _lib = lib
         return lib
 
@@ -126,6 +129,9 @@ class OracleSim:
         if wall_vel is not None:
             self._wv = np.ascontiguousarray(np.asarray(wall_vel, dtype=np.float64).reshape(18))
             lib.orc_set_wall_velocity(self.h, _dp(self._wv))
+        rd = getattr(sc, "readings", None)
+        if rd is not None:
+            self.set_readings(**rd)
         for b in sc.boxes:
             self.add_box(b)
 
@@ -139,8 +145,22 @@ class OracleSim:
             self.lib.orc_destroy(self.h)
             self.h = None
 
+    def set_readings(self, deadband: float = 1e-3, virtual_mass: float = 1.0, force_mean: bool = True,
+                     neighbour_rule: bool = True):
+        """The options where the paper is silent (C declaration of orc_set_readings)."""
+        self.lib.orc_set_readings(self.h, float(deadband), float(virtual_mass), int(bool(force_mean)),
+                                  int(bool(neighbour_rule)))
+
     def step(self, n: int = 1) -> int:
         return self.lib.orc_step(self.h, int(n))
+
+    def set_body_force(self, b: int, F, T):
+        """Force and torque of body b as if the momentum exchange had produced them."""
+        self.lib.orc_set_body_force(self.h, int(b), _d3(F), _d3(T))
+
+    def bodies_step(self):
+        """The rigid-body update alone (no fluid step, no remapping)."""
+        self.lib.orc_bodies_step(self.h)
 
     def compute_forces(self):
         self.lib.orc_compute_forces(self.h)

@@ -135,6 +135,11 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     for (int f = 0; f < 6; ++f)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(p->wall_vel[f][k])) return fail(LBM_FS_EINVAL, "non-finite wall velocity%s");
+    const bool rd_db = p->readings & LBM_FS_READING_DEADBAND, rd_vm = p->readings & LBM_FS_READING_VIRTUAL_MASS;
+    if (rd_db && !(p->normal_deadband >= 0.0 && std::isfinite(p->normal_deadband)))
+        return fail(LBM_FS_EINVAL, "normal_deadband must be finite and >= 0%s");
+    if (rd_vm && !(p->virtual_mass >= 0.0 && std::isfinite(p->virtual_mass)))
+        return fail(LBM_FS_EINVAL, "virtual_mass must be finite and >= 0%s");
     double proj = 0.0;
     for (int k = 0; k < 3; ++k) {
         double a = fabs(p->gravity[k] + p->body_accel[k]);
@@ -184,6 +189,11 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.sigma = p->sigma;
     d.sigma_f = (float)p->sigma;
     d.cap = (uint32_t)N;
+    d.deadband = rd_db ? p->normal_deadband : 1e-3;
+    d.deadband_f = (float)d.deadband;
+    d.vmass = rd_vm ? p->virtual_mass : 1.0;
+    d.force_mean = (p->readings & LBM_FS_READING_FORCE_MEAN) ? (p->force_mean != 0) : 1;
+    d.nb_rule = (p->readings & LBM_FS_READING_NEIGHBOUR_RULE) ? (p->neighbour_rule != 0) : 1;
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
     // bulk-kernel variant (float storages): direct loads by default;
     // LBMFS_BULK=pipe|tma selects the shared-memory staged variants (both

@@ -82,6 +82,12 @@ struct Dev {
     // highest z-plane of a bulk tile holding liquid or interface cells: read
     // (previous step) and written (this step) slots, swapped every step
     int *ztop_rd, *ztop_wr;
+    // readings where the paper is silent (lbm_fs_params.readings)
+    double deadband;   // Eq. reconstruct: c.n < -deadband selects a direction
+    float deadband_f;
+    double vmass;      // virtual-mass coefficient of the rigid-body update
+    int force_mean;    // rigid-body update driven by (F_n + F_{n-1}) / 2
+    int nb_rule;       // interface cells without liquid (gas) neighbours empty (fill)
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,

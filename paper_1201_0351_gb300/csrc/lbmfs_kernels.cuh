@@ -59,10 +59,6 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
     return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
 
-// Eq. reconstruct selects c_q . n <= 0; tangential directions of a flat
-// surface sit at c.n = 0 up to noise, so only c.n < -1e-3 counts
-constexpr double NORMAL_DEADBAND = 1e-3;
-constexpr double VIRTUAL_MASS = 1.0;      // rigid-body update, Schwarz et al. 2015
 #ifndef LBMFS_BULK_MINB
 #define LBMFS_BULK_MINB 8  // resident blocks per SM asked of ptxas for the bulk kernel (64 registers)
 #endif
@@ -1775,7 +1771,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
-                if (cn < -NORMAL_DEADBAND && scl[q] != CL_O && scl[q] != CL_WALL) {
+                if (cn < -d.deadband && scl[q] != CL_O && scl[q] != CL_WALL) {
                     int qb = opp(q);
                     fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
                 }
@@ -1809,7 +1805,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
             // an interface cell without a liquid neighbour empties, one without
             // a gas neighbour fills
-            if (!mk) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
+            if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
             if (mk) d.cmark[i] = mk;
             wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
@@ -1887,7 +1883,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const float cn = cx(q) * nv0 + cy(q) * nv1 + cz(q) * nv2;
-                if ((gas & (1u << q)) || (cn < -(float)NORMAL_DEADBAND && !(solid & (1u << q)))) {
+                if ((gas & (1u << q)) || (cn < -d.deadband_f && !(solid & (1u << q)))) {
                     const int qb = opp(q);
                     fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
                 }
@@ -1906,7 +1902,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             d.phidst[i] = phin;
             if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
             uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
-            if (!mk) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
+            if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
             if (mk) d.cmark[i] = mk;
             wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
             wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
@@ -2228,13 +2224,15 @@ __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *a
         return;
     }
     // the update is driven by the mean of this step's and the previous step's
-    // force and torque (the force alone on the first step): near tau = 1/2 a
+    // force and torque (the force alone on the first step; the force alone
+    // throughout when the two-step mean is switched off): near tau = 1/2 a
     // force that flips sign every step would feed the barely damped BGK modes
     // of that period through the wall velocity
     double Fh[3], Th[3];
+    const bool mean = d.force_mean && b.nF;
     for (int k = 0; k < 3; ++k) {
-        Fh[k] = b.nF ? 0.5 * (b.F[k] + b.Fp[k]) : b.F[k];
-        Th[k] = b.nF ? 0.5 * (b.T[k] + b.Tp[k]) : b.T[k];
+        Fh[k] = mean ? 0.5 * (b.F[k] + b.Fp[k]) : b.F[k];
+        Th[k] = mean ? 0.5 * (b.T[k] + b.Tp[k]) : b.T[k];
         b.Fp[k] = b.F[k];
         b.Tp[k] = b.T[k];
     }
@@ -2252,9 +2250,10 @@ __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *a
         I[2] = (mass / 3.0) * (b.h[0] * b.h[0] + b.h[1] * b.h[1]);
     }
     double If[3] = {I[0] / b.dens, I[1] / b.dens, I[2] / b.dens};
-    double den = mass + VIRTUAL_MASS * vol;
+    const double C = d.vmass;  // virtual-mass coefficient (Schwarz, Kempe and Froehlich 2015)
+    double den = mass + C * vol;
     for (int k = 0; k < 3; ++k) {
-        double num = (Fh[k] + mass * d.grav[k]) + VIRTUAL_MASS * (vol * b.dv[k]);
+        double num = (Fh[k] + mass * d.grav[k]) + C * (vol * b.dv[k]);
         b.dv[k] = num / den;
         b.v[k] = b.v[k] + b.dv[k];
     }
@@ -2270,7 +2269,7 @@ __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *a
         double Ia = (ab[0] * ab[0] * I[0] + ab[1] * ab[1] * I[1]) + ab[2] * ab[2] * I[2];
         double Ifa = Ia / b.dens;
         double ws = (b.w[0] * ax[0] + b.w[1] * ax[1]) + b.w[2] * ax[2];
-        b.dw[0] = (ta + VIRTUAL_MASS * (Ifa * b.dw[0])) / (Ia + VIRTUAL_MASS * Ifa);
+        b.dw[0] = (ta + C * (Ifa * b.dw[0])) / (Ia + C * Ifa);
         ws = ws + b.dw[0];
         for (int k = 0; k < 3; ++k) b.w[k] = ws * ax[k];
     } else {
@@ -2284,7 +2283,7 @@ __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *a
         gy[1] = wb[2] * L[0] - wb[0] * L[2];
         gy[2] = wb[0] * L[1] - wb[1] * L[0];
         for (int k = 0; k < 3; ++k) {
-            b.dw[k] = ((tb[k] - gy[k]) + VIRTUAL_MASS * (If[k] * b.dw[k])) / (I[k] + VIRTUAL_MASS * If[k]);
+            b.dw[k] = ((tb[k] - gy[k]) + C * (If[k] * b.dw[k])) / (I[k] + C * If[k]);
             wb[k] = wb[k] + b.dw[k];
         }
         for (int k = 0; k < 3; ++k) b.w[k] = (R[k * 3 + 0] * wb[0] + R[k * 3 + 1] * wb[1]) + R[k * 3 + 2] * wb[2];

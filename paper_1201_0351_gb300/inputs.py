@@ -99,6 +99,9 @@ class Scenario:
     vel: Optional[np.ndarray] = None  # float64[3N] (xyz per cell) or None = at rest
     sigma: float = 0.0  # surface tension (Laplace pressure 2 sigma kappa at the interface); 0 = none
     wall_vel: Optional[tuple] = None  # 18 floats: velocity of the faces x-, x+, y-, y+, z-, z+; None = at rest
+    # options where the paper is silent, as keyword values (deadband, virtual_mass,
+    # force_mean, neighbour_rule); None = each side's defaults (1e-3, 1, True, True)
+    readings: Optional[dict] = None
 
     @property
     def n_cells(self) -> int:
@@ -398,24 +401,31 @@ def droplet(n: int = 30, radius: float = 7.0, sigma: float = 4e-3, tau: float = 
                     fill.astype(np.float64), rho, [], 400, sigma=sigma)
 
 
-def floating_cubes(steps: int = 40000) -> Scenario:
+def floating_cubes(steps: int = 40000, free_rotation: bool = False, scale: int = 1,
+                   damping: float = 0.0) -> Scenario:
     """The floating-cube equilibrium of Sec. 3.2.2: a 130x40x40 basin filled to
     half height, tau 1/1.9, g 7.5e-4, three 32x16x16 boxes (the 2D cube of side
     s = 16 extended to 2s along its rolling axis x) of densities 0.75, 0.5 and
-    0.25, free to roll about x only and to translate, placed at the draft of
-    their 2.86 deg initial heel.  Stable heels: atan(1/2) = 26.565 deg for 0.25
-    and 0.75, 45 deg for 0.5."""
-    nx, ny, nz = 130, 40, 40
-    g, eta, s = 7.5e-4, 20.0, 16.0
+    0.25, placed at the draft of their 2.86 deg initial heel.  Rotation about
+    x only, or free in all three axes (free_rotation); damping > 0 damps the
+    translation by that fraction per step.  scale > 1 refines the lattice
+    (every length times scale, g / scale so that the hydrostatic density
+    variation 3 g depth stays the same).  Stable heels: atan(1/2) = 26.565 deg
+    for 0.25 and 0.75, 45 deg for 0.5."""
+    nx, ny, nz = 130 * scale, 40 * scale, 40 * scale
+    g, eta, s = 7.5e-4 / scale, 20.0 * scale, 16.0 * scale
     flags, fill, rho = hydrostatic_tank(nx, ny, nz, lambda X, Y: eta, g, 1.0, 0)
+    mode = MODE_FREE if free_rotation else MODE_ROT_AXIS_ONLY
+    if damping > 0.0:
+        mode |= MODE_DAMP_TRANSLATION
     boxes = []
     for k, dens in enumerate((0.75, 0.5, 0.25)):
         heel = 2.86
         zc = eta + immersed_offset(s, s, math.radians(heel), dens)
         boxes.append(Box(center=(nx * (2 * k + 1) / 6.0, ny / 2.0, zc), half=(s, s / 2, s / 2), quat=heel_quat(heel),
-                         density_ratio=dens, mode=MODE_ROT_AXIS_ONLY, rot_axis=(1.0, 0.0, 0.0)))
-    return Scenario("floating_cubes_130x40x40", nx, ny, nz, 0, 1.0 / 1.9, (0.0, 0.0, -g), (0.0, 0.0, 0.0), 1.0, 1e-2,
-                    flags, fill, rho, boxes, steps)
+                         density_ratio=dens, mode=mode, rot_axis=(1.0, 0.0, 0.0), lin_damping=damping))
+    return Scenario("floating_cubes_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, 0, 1.0 / 1.9, (0.0, 0.0, -g),
+                    (0.0, 0.0, 0.0), 1.0, 1e-2, flags, fill, rho, boxes, steps)
 
 
 def free_advection_channel(tau: float = 0.8, u: float = 1e-4, g: float = 1e-5, steps: int = 20000,

@@ -35,7 +35,16 @@ class lbm_fs_params(C.Structure):
                 ("init_vel", C.c_void_p), ("init_on_device", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p), ("use_graphs", C.c_int32), ("sigma", C.c_double),
-                ("wall_vel", C.c_double * 18)]
+                ("wall_vel", C.c_double * 18), ("readings", C.c_uint32), ("normal_deadband", C.c_double),
+                ("virtual_mass", C.c_double), ("force_mean", C.c_int32), ("neighbour_rule", C.c_int32)]
+
+
+# bits of lbm_fs_params.readings, and the scenario keyword each one serves
+READING_DEADBAND, READING_VIRTUAL_MASS, READING_FORCE_MEAN, READING_NEIGHBOUR_RULE = 1, 2, 4, 8
+READINGS = {"deadband": ("normal_deadband", READING_DEADBAND, float),
+            "virtual_mass": ("virtual_mass", READING_VIRTUAL_MASS, float),
+            "force_mean": ("force_mean", READING_FORCE_MEAN, lambda v: int(bool(v))),
+            "neighbour_rule": ("neighbour_rule", READING_NEIGHBOUR_RULE, lambda v: int(bool(v)))}
 
 
 class lbm_fs_box(C.Structure):
@@ -352,6 +361,10 @@ def scenario_params(sc, storage: str, stream: int, use_graphs: bool, alloc=None,
     wall_vel = getattr(sc, "wall_vel", None)
     if wall_vel is not None:
         p.wall_vel[:] = [float(v) for v in np.asarray(wall_vel, dtype=np.float64).reshape(18)]
+    for key, value in (getattr(sc, "readings", None) or {}).items():
+        field, bit, conv = READINGS[key]
+        setattr(p, field, conv(value))
+        p.readings |= bit
     return p
 
 

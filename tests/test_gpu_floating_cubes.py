@@ -3,43 +3,65 @@
 0.5 and 0.25 start 2.86 deg off upright in a half-filled 130x40x40 basin
 (tau 1/1.9, g 7.5e-4) and roll towards their stable heels: 45 deg for 0.5 and
 atan(1/2) = 26.565 deg for 0.25 and 0.75 (modulo the square's 90 deg
-symmetry and its mirror).  Far too long for the oracle, so the GPU is checked
-against these closed-form angles.
+symmetry and its mirror).
 
-The build has no body-wall contact model, so the boxes' translation is damped
-by 1 % per step to keep them off the side walls (a free box drifts towards a
-wall within ~1e4 steps and the library then stops with a contact error);
-damping the translation does not move the equilibrium heel.  At this
-resolution (16 cells per side) the 0.5 and 0.25 boxes settle within a few
-degrees of the ideal angles; the 0.75 box, 12 of its 16 cells submerged,
-settles about 9 deg high, which the looser bound records."""
-import dataclasses
+The first 200 steps of the basin, with rotation about x only and with free
+rotation in all three axes, are checked against the oracle (FP64 parity).  The
+long run is far too long for the oracle, so the GPU is checked against the
+closed-form angles.  The build has no body-wall contact model, so the boxes'
+translation is damped by 1 % per step to keep them off the side walls (a free
+box drifts towards a wall within ~1e4 steps and the library then stops with a
+contact error); damping the translation does not move the equilibrium heel.
+At this resolution (16 cells per side) the 0.5 and 0.25 boxes settle within a
+few degrees of the ideal angles; the 0.75 box, 12 of its 16 cells submerged,
+settles about 9 deg high, which its looser bound records."""
 import math
 
+import numpy as np
 import pytest
 
 from paper_1201_0351_gb300 import inputs as I
 
+from parity import assert_f64_parity, run_both
+
 pytestmark = pytest.mark.gpu
 
 
-def _heel(state):
-    a = abs(math.degrees(2.0 * math.atan2(state["quat"][1], state["quat"][0]))) % 90.0
+def _roll(q):
+    """roll about x (deg), folded by the square's 90 deg symmetry and mirror"""
+    w, x, y, z = q
+    a = abs(math.degrees(math.atan2(2 * (y * z + w * x), 1 - 2 * (x * x + y * y)))) % 90.0
     return min(a, 90.0 - a)
 
 
+def _tilt(q):
+    """angle (deg) between the body's long axis and the world x axis"""
+    w, x, y, z = q
+    return math.degrees(math.acos(min(1.0, abs(1 - 2 * (y * y + z * z)))))
+
+
+@pytest.mark.parametrize("free_rotation", [False, True])
+def test_floating_cubes_first_200_steps_match_oracle(free_rotation):
+    sc = I.floating_cubes(free_rotation=free_rotation, damping=0.01)
+    g, o, gb, ob, gs, _ = run_both(sc, 200)
+    assert_f64_parity(g, o, gb, ob)
+
+
 def test_floating_cubes_reach_stable_heels():
+    """free rotation in all three axes: the boxes roll about their long axis
+    to the stable heels and stay aligned with it"""
     from paper_1201_0351_gb300 import lbm_fs
 
-    sc = I.floating_cubes()
-    sc = dataclasses.replace(sc, boxes=[dataclasses.replace(b, mode=b.mode | I.MODE_DAMP_TRANSLATION,
-                                                            lin_damping=0.01) for b in sc.boxes])
+    sc = I.floating_cubes(free_rotation=True, damping=0.01)
     sim = lbm_fs.Simulation(sc, storage="f32")
-    history = []
+    history, tilt = [], []
     for _ in range(4):
         sim.step(6000)
-        history.append([_heel(sim.body(k)) for k in range(3)])
+        qs = [sim.body(k)["quat"] for k in range(3)]
+        history.append([_roll(q) for q in qs])
+        tilt.append([_tilt(q) for q in qs])
     sim.close()
+    print("roll", history, "tilt of the long axis", tilt)
     final = history[-1]
     ideal = math.degrees(math.atan(0.5))
     assert abs(final[1] - 45.0) <= 3.0, history          # density 0.5
@@ -47,3 +69,4 @@ def test_floating_cubes_reach_stable_heels():
     assert abs(final[0] - ideal) <= 10.0, history        # density 0.75 (coarse)
     # all three left the (unstable for 0.5) near-upright start
     assert min(h[1] for h in history[1:]) > 30.0, history
+    assert max(max(t) for t in tilt) < 2.0, tilt

@@ -248,3 +248,44 @@ def test_neighbour_rule_mutation_is_caught():
     finally:
         oracle.set_mutation(0)
     assert flag == I.INTERFACE
+
+
+def test_new_interface_cell_takes_the_mean_state_of_its_fluid_neighbours():
+    """Sec. 2.2 (reading R8): a gas cell next to a filled cell becomes interface
+    with f = f_eq(rho_bar, u_bar), the means over its neighbours that were
+    liquid or interface before the conversion (not gas, not the other new
+    cells), with each neighbour's velocity that of its last collision,
+    u = sum c f / rho - a.  Checked by brute force on a moving surface layer
+    with random densities and velocities under gravity, so a wrong neighbour
+    set, a velocity without the -a, or a weighted mean all show."""
+    n = 8
+    rng = np.random.default_rng(11)
+    flags, fill, rho = _layered(n, 3)
+    fill[3, 3, 3] = 1.6
+    rho = 1.0 + 0.02 * (rng.random((n, n, n)) - 0.5)
+    vel = 2e-3 * (rng.random((n, n, n, 3)) - 0.5)
+    a = np.array([0.0, 0.0, -1e-4])
+    sc = I.Scenario("newg", n, n, n, 3, 0.7, tuple(a), (0.0, 0.0, 0.0), 1.0, 1e-2, flags.reshape(-1).copy(),
+                    fill.reshape(-1).copy(), rho.reshape(-1).copy(), [], 0, vel=vel.reshape(-1).copy())
+    s = oracle.OracleSim(sc)
+    s.step(1)
+    out = s.fields(want_f=True)
+    got = out["flags"].reshape(n, n, n)
+    f = out["f"].reshape(19, n, n, n)
+    c, w, _ = oracle.lattice()
+    new = [(4, 3 + dy, 3 + dx) for dx, dy, dz in NEIGH if dz == 1]
+    assert all(got[p] == I_ for p in new)
+    for (z, y, x) in new:
+        rs, us = [], []
+        for dx, dy, dz in NEIGH:
+            zz, yy, xx = z + dz, (y + dy) % n, (x + dx) % n
+            if not 0 <= zz < n or flags[zz, yy, xx] not in (L_, I_):
+                continue
+            fk = f[:, zz, yy, xx]
+            r = fk.sum()
+            rs.append(r)
+            us.append((c.T @ fk) / r - a)
+        assert len(rs) == 5  # the filled cell and four old interface cells of its layer
+        exp = oracle.feq(np.mean(rs), np.mean(us, axis=0))
+        assert np.abs(f[:, z, y, x] - exp).max() <= 1e-15
+    assert _ledger_ok(s)

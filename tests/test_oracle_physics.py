@@ -1,6 +1,7 @@
 """Pins of the oracle against closed forms, invariants and the paper's theory
 (no GPU).  Each test names the passage it checks.
 """
+import dataclasses
 import math
 import os
 
@@ -39,12 +40,16 @@ def _shear_wave_error(L, tau=0.6, U=1e-3, t_per_L2=1000.0 / 32 ** 2):
 
 
 def test_shear_wave_decay_second_order():
-    """Eq. lbgk + tau = 3 nu + 1/2: a shear wave decays as exp(-nu k^2 t);
-    the error is small and converges at second order in the resolution."""
+    """Eq. lbgk + tau = 3 nu + 1/2: a shear wave decays as exp(-nu k^2 t).  The
+    lattice's own error is second order in the resolution: it falls by 4 from
+    L = 32 to L = 64 (the same diffusive time), and the Richardson extrapolation
+    (4 e64 - e32) / 3 removes it to below 1e-4 (a dropped or wrong term in the
+    collision would leave an error that does not extrapolate away)."""
     e32 = _shear_wave_error(32)
     e64 = _shear_wave_error(64)
-    assert abs(e32) < 1.5e-2
-    assert abs(e64) < abs(e32) / 3.0
+    assert abs(e32) < 1e-2
+    assert 3.5 < e32 / e64 < 4.5
+    assert abs((4.0 * e64 - e32) / 3.0) < 1e-4
 
 
 def test_uniform_flow_is_preserved():
@@ -79,18 +84,47 @@ def test_hydrostatic_profile_sign_and_slope():
     assert s.error == 0
 
 
-def test_planar_surface_stays_planar():
-    """Sec. 3.2.1: a planar free surface remains planar, spurious interface
-    velocities stay of the order of g."""
-    s = oracle.OracleSim(I.closed_tank_32(with_box=False))
-    s.step(200)
+def _planar(sc, steps, deadband=None):
+    if deadband is not None:
+        sc = dataclasses.replace(sc, readings=dict(deadband=deadband))
+    s = oracle.OracleSim(sc)
+    s.step(steps)
     f = s.fields()
-    flags = f["flags"].reshape(32, 32, 32)
-    zs = np.unique(np.nonzero(flags == I.INTERFACE)[0])
-    assert list(zs) == [16]
-    fill = f["fill"].reshape(32, 32, 32)[16]
-    assert np.ptp(fill) < 3e-3  # height variation of the surface, in cells
-    assert np.abs(f["u"]).max() < 1e-4
+    sh = (sc.nz, sc.ny, sc.nx)
+    flags = f["flags"].reshape(sh)
+    ifc = flags == I.INTERFACE
+    u = f["u"].reshape(sh + (3,))
+    bulk = u[flags == I.LIQUID].mean(axis=0)
+    return (np.unique(np.nonzero(ifc)[0]), np.ptp(f["fill"].reshape(sh)[ifc]), np.abs(u[ifc] - bulk).max(),
+            s.error)
+
+
+def test_planar_surface_stays_planar():
+    """Sec. 3.2.1: a planar free surface remains planar and the spurious
+    interface velocities (deviation from the bulk velocity) stay below 1e-5 --
+    in a closed tank at rest (tau 0.6, below the paper's lowest tau) and in the
+    paper's channel (60 x 40 x 30, surface 19.5, walls moving with u = 1e-4,
+    g = 1e-5, tau = 0.62)."""
+    zs, spread, dev, err = _planar(I.closed_tank_32(with_box=False), 200)
+    assert list(zs) == [16] and err == 0
+    assert spread < 1e-3  # height variation of the surface, in cells
+    assert dev < 1e-5
+    ch = dataclasses.replace(I.free_advection_channel(tau=0.62, u=1e-4), boxes=[])
+    zs, spread, dev, err = _planar(ch, 150)
+    assert list(zs) == [19] and err == 0
+    assert spread < 1e-3 and dev < 1e-5
+
+
+def test_strict_sign_test_breaks_the_planar_bound():
+    """The reading of Eq. reconstruct's c.n <= 0 set: with the bare sign test
+    (dead band 0) the noise of the estimated normal decides the tangential
+    directions of a flat surface cell by cell, and the spurious interface
+    velocities of the same closed tank exceed the paper's 1e-5 several times
+    over (measured 7e-5); with the 1e-3 dead band they stay below it (previous
+    test).  The surface stays one layer thick either way."""
+    zs, spread, dev, err = _planar(I.closed_tank_32(with_box=False), 200, deadband=0.0)
+    assert list(zs) == [16] and err == 0
+    assert dev > 2e-5
 
 
 # ----------------------------------------------------------- Sec. 2.2
@@ -109,9 +143,12 @@ def test_closed_tank_mass_conservation():
     assert s.error == 0
 
 
-def _duct(H=16.5, nz=20, tau=0.8, a=1e-6, steps=8000):
+def _duct(H=16.5, nz=20, tau=0.8, a=1e-6, steps=8000, deadband=None):
     fl, fi, rh = I.hydrostatic_tank(4, 4, nz, lambda X, Y: H, 0.0, 1.0, 3)
-    s = oracle.OracleSim(_scenario(4, 4, nz, 3, tau, fl, fi, rh, body_accel=(a, 0.0, 0.0)))
+    sc = _scenario(4, 4, nz, 3, tau, fl, fi, rh, body_accel=(a, 0.0, 0.0))
+    if deadband is not None:
+        sc = dataclasses.replace(sc, readings=dict(deadband=deadband))
+    s = oracle.OracleSim(sc)
     s.step(steps)
     f = s.fields()
     u = f["u"].reshape(nz, 4, 4, 3)[:, 0, 0, 0]
@@ -119,14 +156,17 @@ def _duct(H=16.5, nz=20, tau=0.8, a=1e-6, steps=8000):
     return u, flags, (tau - 0.5) / 3.0
 
 
-def test_gravity_driven_layer_profile():
+@pytest.mark.parametrize("deadband", [None, 0.0])
+def test_gravity_driven_layer_profile(deadband):
     """Sec. 2.2 free-surface condition (Eq. reconstruct): a liquid layer driven
     along x over a no-slip floor has the half-Poiseuille profile
     u = (a / nu)(H z - z^2 / 2).  The stress-free plane of the anti-bounce-back
     lies half-way between the interface cell and the gas cell above it (z = 17
-    for the interface layer at z = 16); the curvature u'' = -a / nu is exact."""
+    for the interface layer at z = 16); the curvature u'' = -a / nu is exact.
+    Holds with the default dead band and with the bare sign test of the
+    paper's c.n <= 0 set (the flat layer's normal has no tangential noise)."""
     a = 1e-6
-    u, flags, nu = _duct(a=a)
+    u, flags, nu = _duct(a=a, deadband=deadband)
     z = np.arange(20) + 0.5
     liq = flags == I.LIQUID
     ex = a / nu * (17.0 * z - z * z / 2.0)
@@ -312,6 +352,30 @@ def test_archimedes_converges_with_resolution():
         assert np.abs(b["F"][:2]).max() <= 1e-12 * b["S"]
     assert 0 < errs[0] < 0.3
     assert 0 < errs[1] < 0.7 * errs[0]
+
+
+def test_closed_tank_box_force_after_200_steps():
+    """The 32^3 closed tank with the fixed 8 x 8 x 6 box half immersed: at rest
+    the liquid stays hydrostatic, so after 200 steps the buoyancy equals the
+    exact t = 0 line sum of Eq. momentumexchange / momentuminterface within 1 %
+    and the lateral force vanishes (below 1e-3 of F_z).  Against Archimedes'
+    rho g V_displaced (V = 8 * 8 * 3.5 below the surface plane 16.5) the force
+    is high by the half-cell offset of the half-way bounce-back pressure (the
+    head is measured at the fluid cell centre half a cell below the box's
+    floor, and the diagonal lines add one cell each), a first-order staircase
+    error that the resolution test above shows shrinking."""
+    sc = I.closed_tank_32()
+    s0 = oracle.OracleSim(sc)
+    s0.compute_forces()
+    f0 = s0.body(0)["F"][2]
+    s = oracle.OracleSim(sc)
+    s.step(200)
+    b = s.body(0)
+    assert b["F"][2] == pytest.approx(f0, rel=1e-2)
+    assert np.abs(b["F"][:2]).max() < 1e-3 * b["F"][2]
+    arch = 1e-5 * 8 * 8 * 3.5
+    assert 1.0 < b["F"][2] / arch < 1.25
+    assert s.error == 0
 
 
 def test_buoyancy_linear_in_level():
