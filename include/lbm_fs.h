@@ -100,7 +100,9 @@ typedef struct {
     const double *init_vel;
     int32_t init_on_device; /* nonzero: the four init pointers are device pointers */
     /* device memory: dev_alloc / dev_free with alloc_ctx (e.g. a framework's
-     * caching allocator); NULL -> cudaMalloc / cudaFree */
+     * caching allocator); NULL -> cudaMalloc / cudaFree.  dev_alloc must
+     * return 16-byte aligned memory (the kernels use vector loads); a
+     * misaligned block gives LBM_FS_EINVAL */
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, void *ctx);
     void *alloc_ctx;

@@ -80,6 +80,7 @@ typedef struct {
     int mode;
     double axis[3], damp;
     double F[3], T[3], S;
+    unsigned __int128 acc[7]; /* fixed-point sums of F, T, S (orc_compute_forces) */
     double dv[3], dw[3]; /* last velocity / angular-velocity increments (virtual mass) */
     double Fp[3], Tp[3]; /* the previous step's force and torque */
     int nF;              /* 1 once Fp, Tp hold a step */
@@ -407,16 +408,35 @@ int orc_add_box(orc_sim *s, const double center[3], const double half[3], const 
 
 /* ------------------------------------------------------------------ C4 */
 
+/* The sums of Eqs. netforce and torque evaluated exactly: every term t
+ * (|t| < 2^31) is written as the integer floor(t 2^96) -- its bits below 2^-96
+ * dropped -- and the integers are added (two's complement, 128 bits), so the
+ * sum does not depend on the order of the terms; the total v = H 2^64 + L
+ * (H signed, L unsigned) is returned as H 2^-32 + L 2^-96 in double. */
+static unsigned __int128 fixed96(double t) {
+    double sc = t * 4294967296.0; /* t 2^32, exact */
+    double hf = floor(sc);
+    long long hi = (long long)hf;
+    unsigned long long lo = (unsigned long long)((sc - hf) * 18446744073709551616.0);
+    return ((unsigned __int128)(unsigned long long)hi << 64) | (unsigned __int128)lo;
+}
+
+static double fixed96_value(unsigned __int128 v) {
+    long long H = (long long)(unsigned long long)(v >> 64);
+    unsigned long long L = (unsigned long long)v;
+    return (double)H * 2.3283064365386962890625e-10 + (double)L * 1.2621774483536188886587657044524580e-29;
+}
+
 /* Momentum exchange (Eqs. momentumexchange, momentuminterface) summed over
  * the links of every non-obstacle cell into a body, and the torque about the
  * body centre with the lever arm from the centre of the cell (Eq. torque).
- * Force on the body = -(momentum gained by the fluid): c_qbar * 2(...). */
+ * Force on the body = -(momentum gained by the fluid): c_qbar * 2(...).  The
+ * sums are exact (fixed96). */
 void orc_compute_forces(orc_sim *s) {
     init_lattice();
     for (int bi = 0; bi < s->nb; ++bi) {
         body_t *b = &s->b[bi];
-        for (int k = 0; k < 3; ++k) b->F[k] = b->T[k] = 0.0;
-        b->S = 0.0;
+        for (int k = 0; k < 7; ++k) b->acc[k] = 0;
     }
     for (int z = 0; z < s->nz; ++z)
         for (int y = 0; y < s->ny; ++y)
@@ -449,15 +469,23 @@ void orc_compute_forces(orc_sim *s) {
                     double Fl[3] = {C[qb][0] * g, C[qb][1] * g, C[qb][2] * g};
                     double r[3] = {min_image(s, (x + 0.5) - b->o[0], 0), min_image(s, (y + 0.5) - b->o[1], 1),
                                    min_image(s, (z + 0.5) - b->o[2], 2)};
-                    b->F[0] += Fl[0];
-                    b->F[1] += Fl[1];
-                    b->F[2] += Fl[2];
-                    b->T[0] += r[1] * Fl[2] - r[2] * Fl[1];
-                    b->T[1] += r[2] * Fl[0] - r[0] * Fl[2];
-                    b->T[2] += r[0] * Fl[1] - r[1] * Fl[0];
-                    b->S += fabs(g);
+                    b->acc[0] += fixed96(Fl[0]);
+                    b->acc[1] += fixed96(Fl[1]);
+                    b->acc[2] += fixed96(Fl[2]);
+                    b->acc[3] += fixed96(r[1] * Fl[2] - r[2] * Fl[1]);
+                    b->acc[4] += fixed96(r[2] * Fl[0] - r[0] * Fl[2]);
+                    b->acc[5] += fixed96(r[0] * Fl[1] - r[1] * Fl[0]);
+                    b->acc[6] += fixed96(fabs(g));
                 }
             }
+    for (int bi = 0; bi < s->nb; ++bi) {
+        body_t *b = &s->b[bi];
+        for (int k = 0; k < 3; ++k) {
+            b->F[k] = fixed96_value(b->acc[k]);
+            b->T[k] = fixed96_value(b->acc[3 + k]);
+        }
+        b->S = fixed96_value(b->acc[6]);
+    }
 }
 
 /* ------------------------------------------------------------- C1 + C2 */

@@ -222,7 +222,8 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     for (int k = 0; k < WL_COUNT; ++k) d.list[k] = (uint32_t *)h->alloc(N * 4);
     d.cnt = (uint32_t *)h->alloc(WL_COUNT * 4);
     d.bodies = (Body *)h->alloc(sizeof(Body) * MAX_BODIES);
-    d.part = (double *)h->alloc(sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7);
+    d.part = (double *)h->alloc(2 * sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7);
+    d.part128 = p->storage == LBM_FS_F64;
     d.ledger = (double *)h->alloc(sizeof(double) * LG_COUNT);
     d.status = (uint32_t *)h->alloc(4);
     d.rdec = (uint8_t *)h->alloc(nb4);
@@ -235,6 +236,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     for (void *ptr : h->allocs)
         if (!ptr) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
     if (h->allocs.size() != 19 + WL_COUNT) return bail(fail(LBM_FS_ENOMEM, "device allocation failed%s"));
+    if (h->misaligned) return bail(fail(LBM_FS_EINVAL, "dev_alloc must return 16-byte aligned memory%s"));
     d.walls_move = 0;
     for (int f = 0; f < 6; ++f)
         for (int k = 0; k < 3; ++k)
@@ -254,7 +256,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     CKB(cudaMemsetAsync(d.cnt, 0, WL_COUNT * 4, st));
     CKB(cudaMemsetAsync(d.ledger, 0, sizeof(double) * LG_COUNT, st));
     CKB(cudaMemsetAsync(d.status, 0, 4, st));
-    CKB(cudaMemsetAsync(d.part, 0, sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7, st));
+    CKB(cudaMemsetAsync(d.part, 0, 2 * sizeof(double) * MAX_BODIES * FORCE_BLOCKS * 7, st));
     CKB(cudaMemcpyAsync(wallv, &p->wall_vel[0][0], sizeof(double) * 18, cudaMemcpyHostToDevice, st));
     // the first step visits every tile (its read slot: nz) and records the top
     const int zt0[2] = {p->nz, -1};

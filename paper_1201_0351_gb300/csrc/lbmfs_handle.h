@@ -25,6 +25,7 @@ struct lbm_fs {
     int graph_nb = -1;
     bool dead = false;
     lbm_fs_batch *owner = nullptr;  // set while the tank belongs to a batch
+    bool misaligned = false;        // a dev_alloc result was not 16-byte aligned
 
     void *alloc(size_t bytes) {
         void *ptr = nullptr;
@@ -36,6 +37,7 @@ struct lbm_fs {
             ptr = nullptr;
         }
         if (ptr) allocs.push_back(ptr);
+        if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 15u)) misaligned = true;  // vector loads need 16 bytes
         return ptr;
     }
     void release() {

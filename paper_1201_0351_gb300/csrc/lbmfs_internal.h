@@ -20,6 +20,9 @@ constexpr int GRID_GUARD = 1024;
 #define LBMFS_BULK_THREADS 128
 #endif
 constexpr int BULK_THREADS = LBMFS_BULK_THREADS;  // x extent of a bulk-kernel block
+// cells of an xy-plane per bulk-kernel block, by storage: one per thread for
+// double, two per thread for the float storages
+constexpr int BULK_CELLS[3] = {BULK_THREADS, 2 * BULK_THREADS, 2 * BULK_THREADS};
 
 // cell classes (as in the C ABI) in the low nibble of the flag byte; bit 4
 // marks a cell with an obstacle or a wall among its 18 neighbours
@@ -65,7 +68,8 @@ struct Dev {
     uint32_t cap;
     Body *bodies;
     int nb;
-    double *part;   // nb * FORCE_BLOCKS * 7
+    double *part;   // force partials: MAX_BODIES * FORCE_BLOCKS * 7 slots of 16 bytes
+    int part128;    // partials are exact 128-bit fixed-point sums (double storage)
     double *ledger; // LG_COUNT
     uint32_t *status;
     uint8_t *rdec;  // remap scratch: decision per pending item
@@ -149,6 +153,7 @@ struct KernelSet {
     int (*bulk_blocks_per_sm)();
     int nkernels;
     const char *const *names;
+    int bulk_cells;  // cells of an xy-plane per bulk-kernel block
 };
 
 // The rigid-body update (double precision, independent of the storage) is

@@ -62,6 +62,9 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 #ifndef LBMFS_BULK_MINB
 #define LBMFS_BULK_MINB 8  // resident blocks per SM asked of ptxas for the bulk kernel (64 registers)
 #endif
+#ifndef LBMFS_PAIR_MINB
+#define LBMFS_PAIR_MINB 5  // resident blocks per SM of the two-cell bulk kernel (float storages, 96 registers)
+#endif
 #ifndef LBMFS_BULK_ZB
 #define LBMFS_BULK_ZB 4    // z-planes per bulk-kernel block
 #endif
@@ -176,6 +179,26 @@ template <> struct Sto<1> {
     static __device__ __forceinline__ float st_raw(void *g, int q, long long i, long long N, float v) {
         return st_one(g, q, i, N, v);
     }
+    // the populations q of the cells j, j + 1 (one 8-byte load when the pair
+    // starts on an even element, two loads otherwise), through the read-only path
+    static __device__ __forceinline__ float2 ldg_pair_raw(const void *g, int q, long long j, long long N) {
+        const long long k = (long long)q * N + j;
+        const float *b = reinterpret_cast<const float *>(g) + k;
+        if (k & 1) return make_float2(pop_ldg(b), pop_ldg(b + 1));
+        return pop_ldg(reinterpret_cast<const float2 *>(b));
+    }
+    // store population q of the cells i, i + 1; returns the values as stored
+    static __device__ __forceinline__ float2 st_pair_raw(void *g, int q, long long i, long long N, float2 v) {
+        const long long k = (long long)q * N + i;
+        float *b = reinterpret_cast<float *>(g) + k;
+        if (k & 1) {
+            pop_st(b, v.x);
+            pop_st(b + 1, v.y);
+        } else {
+            pop_st(reinterpret_cast<float2 *>(b), v);
+        }
+        return v;
+    }
 };
 
 template <> struct Sto<2> {
@@ -245,6 +268,48 @@ template <> struct Sto<2> {
         __half hq = __float2half_rn(v);
         pop_st(const_cast<__half *>(hp(g, N)) + ((long long)(q - 1) * N + i), hq);
         return __half2float(hq);
+    }
+    // the populations q of the cells j, j + 1 in raw units: one 4-byte load
+    // (8 bytes for the rest population) when the pair starts on an even
+    // element, otherwise the two aligned words around it
+    static __device__ __forceinline__ float2 ldg_pair_raw(const void *g, int q, long long j, long long N) {
+        if (q == 0) {
+            const float *b = reinterpret_cast<const float *>(g) + j;
+            if (j & 1) return make_float2(pop_ldg(b), pop_ldg(b + 1));
+            return pop_ldg(reinterpret_cast<const float2 *>(b));
+        }
+        const long long k = (long long)(q - 1) * N + j;
+        const __half *h = hp(g, N) + k;
+        if (k & 1) {
+            const __half2 a = pop_ldg(reinterpret_cast<const __half2 *>(h - 1));
+            const __half2 b = pop_ldg(reinterpret_cast<const __half2 *>(h + 1));
+            return make_float2(__high2float(a), __low2float(b));
+        }
+        return __half22float2(pop_ldg(reinterpret_cast<const __half2 *>(h)));
+    }
+    // store population q of the cells i, i + 1 (raw units); returns the
+    // values as stored
+    static __device__ __forceinline__ float2 st_pair_raw(void *g, int q, long long i, long long N, float2 v) {
+        if (q == 0) {
+            float *b = reinterpret_cast<float *>(g) + i;
+            if (i & 1) {
+                pop_st(b, v.x);
+                pop_st(b + 1, v.y);
+            } else {
+                pop_st(reinterpret_cast<float2 *>(b), v);
+            }
+            return v;
+        }
+        const long long k = (long long)(q - 1) * N + i;
+        __half *h = const_cast<__half *>(hp(g, N)) + k;
+        const __half2 hv = __floats2half2_rn(v.x, v.y);
+        if (k & 1) {
+            pop_st(h, __low2half(hv));
+            pop_st(h + 1, __high2half(hv));
+        } else {
+            pop_st(reinterpret_cast<__half2 *>(h), hv);
+        }
+        return __half22float2(hv);
     }
 };
 
@@ -514,96 +579,94 @@ __device__ __forceinline__ void collide_d(const Dev &d, const double *fp, double
 
 // ----------------------------------------- float arithmetic on deviations
 
-// BGK collision of deviations dp_q = f'_q - w_q -> dn_q; returns rho - 1
-__device__ __forceinline__ float collide_f(const Dev &d, const float *dp, float *dn, float &rho_out) {
-    float dr = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) dr += dp[q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if (cx(q)) j0 += cx(q) * dp[q];
-        if (cy(q)) j1 += cy(q) * dp[q];
-        if (cz(q)) j2 += cz(q) * dp[q];
-    }
-    float rho = 1.0f + dr;
-    float inv = 1.0f / rho;
-    float ux = j0 * inv, uy = j1 * inv, uz = j2 * inv;
-    float usq = ux * ux + uy * uy + uz * uz;
-    float om = d.omega_f;
-    float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
-    float ua = ux * ax + uy * ay + uz * az;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
-        float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
-        float deq = wf(q) * (dr + s + dr * s);  // w (rho (1 + s) - 1)
-        float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
-        float fq = wf(q) * rho * (3.0f * (ca - ua) + 9.0f * cu * ca);
-        dn[q] = dp[q] - om * (dp[q] - deq) + fq;
-    }
-    rho_out = rho;
-    return dr;
-}
+// ---- the same collision for one cell (V = float) or two cells at once
+// (V = float2, GB300's packed FP32 instructions): every operation is written
+// out as one correctly rounded add, multiply or fused multiply-add, so both
+// forms round each cell identically and a cell's result does not depend on
+// whether it was collided alone or in a pair.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+template <class V> __device__ __forceinline__ V vbc(float s);
+template <> __device__ __forceinline__ float vbc<float>(float s) { return s; }
+template <> __device__ __forceinline__ float2 vbc<float2>(float s) { return make_float2(s, s); }
+// a - b as one rounding (b * -1 is exact)
+template <class V> __device__ __forceinline__ V vsub(V a, V b) { return vfma(b, vbc<V>(-1.0f), a); }
+__device__ __forceinline__ bool vpos_finite(float r) { return r > 0.0f && r < 1e30f; }
+__device__ __forceinline__ bool vpos_finite(float2 r) { return vpos_finite(r.x) && vpos_finite(r.y); }
 
-// Collision fused with the store for the float storages: each collided
-// deviation is stored as soon as it is computed, and the rest population is
-// stored as dp_0 + sum_{q>=1} (dp_q - stored_q): equal to the collided rest
+// BGK collision with the Luo force term on deviations dp_q = f'_q - w_q (q >= 1
+// times SC, a power of two: the FP16 storage's own scale; dp_0 unscaled),
+// fused with the store: store(q, dn) writes the collided deviation and returns
+// the value as stored.  The rest population is stored as
+// dp_0 + sum_{q>=1} (dp_q - stored_q) / SC: equal to the collided rest
 // population in exact arithmetic, it makes the stored cell sum equal the
-// streamed-in sum up to one rounding (no mass drift from float rounding).
+// streamed-in sum up to one rounding (no mass drift from storage rounding).
+// For each pair q, qbar the equilibrium and force terms split as
+//   f_eq - w = A +- B,  F = C +- D  with
+//   A = w dr + w rho (4.5 (c.u)^2 - 1.5 u.u),  B = 3 w rho c.u,
+//   C = w rho (9 (c.u)(c.a) - 3 u.a),          D = 3 w rho c.a,
+// (c of the pair's member with the positive leading component) so that
+//   dn = (1 - omega) dp + (E +- G),  E = omega A + C,  G = omega B + D.
 // Returns the collision density.
-//
-// SC (a power of two): dp_q for q >= 1 arrive, and are stored, multiplied by
-// SC (the FP16 storage's own scale), dp_0 unscaled.  Every intermediate that
-// carries a population is then SC times the unscaled one; scaling by a power
-// of two adds no rounding, so this is the unscaled collision without a
-// multiplication per load and per store.
-template <int SC = 1, class Store>
-__device__ __forceinline__ float collide_store_f(const Dev &d, const float *dp, Store store) {
+template <int SC, class V, class Store>
+__device__ __forceinline__ V collide_store_v(const Dev &d, const V *dp, Store store) {
     constexpr float sc = (float)SC, isc = 1.0f / (float)SC;
-    float dr = dp[0], j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+    V dr = dp[0];
 #pragma unroll
-    for (int q = 1; q < Q; ++q) dr = fmaf(dp[q], isc, dr);  // exact product: dr + dp_q / SC, one rounding
+    for (int q = 1; q < Q; ++q) dr = vfma(dp[q], vbc<V>(isc), dr);
+    V j0 = vbc<V>(0.0f), j1 = vbc<V>(0.0f), j2 = vbc<V>(0.0f);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if (cx(q)) j0 += cx(q) * dp[q];
-        if (cy(q)) j1 += cy(q) * dp[q];
-        if (cz(q)) j2 += cz(q) * dp[q];
+    for (int q = 1; q < Q; ++q) {
+        if (cx(q) > 0) j0 = vadd(j0, dp[q]);
+        if (cx(q) < 0) j0 = vsub(j0, dp[q]);
+        if (cy(q) > 0) j1 = vadd(j1, dp[q]);
+        if (cy(q) < 0) j1 = vsub(j1, dp[q]);
+        if (cz(q) > 0) j2 = vadd(j2, dp[q]);
+        if (cz(q) < 0) j2 = vsub(j2, dp[q]);
     }
-    const float rho = 1.0f + dr;
-    const float inv = 1.0f / rho;
-    const float ux = (j0 * inv) * isc, uy = (j1 * inv) * isc, uz = (j2 * inv) * isc;
-    const float usq = ux * ux + uy * uy + uz * uz;
+    const V rho = vadd(vbc<V>(1.0f), dr);
+    const V inv = vmul(vrcp(rho), vbc<V>(isc));
+    const V ux = vmul(j0, inv), uy = vmul(j1, inv), uz = vmul(j2, inv);
+    const V nusq15 = vmul(vfma(uz, uz, vfma(uy, uy, vmul(ux, ux))), vbc<V>(-1.5f));  // -1.5 u.u
     const float om = d.omega_f, om1 = 1.0f - om;
     const float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
-    const float ua3 = 3.0f * (ux * ax + uy * ay + uz * az);
-    // per weight class: w dr, w rho, 3 w rho
-    const float wdr1 = (wf(1) * dr) * sc, wr1 = (wf(1) * rho) * sc, wr13 = 3.0f * wr1;
-    const float wdr2 = (wf(7) * dr) * sc, wr2 = (wf(7) * rho) * sc, wr23 = 3.0f * wr2;
-    float rest = 0.0f;
-    // opposite directions q, qbar share everything but the sign of c.u and
-    // c.a: f_eq - w = A +- B, force term = C +- D with
-    //   A = w dr + w rho (4.5 (c.u)^2 - 1.5 u.u),  B = 3 w rho c.u,
-    //   C = w rho (9 (c.u)(c.a) - 3 u.a),          D = 3 w rho c.a,
-    // and the relaxed value (1 - omega) dp + omega f_eq + F splits alike
+    const V nua3 = vmul(vfma(uz, vbc<V>(az), vfma(uy, vbc<V>(ay), vmul(ux, vbc<V>(ax)))), vbc<V>(-3.0f));
+    // per weight class: w dr, w rho, 3 w rho (times SC)
+    const V wdr1 = vmul(dr, vbc<V>(wf(1) * sc)), wr1 = vmul(rho, vbc<V>(wf(1) * sc));
+    const V wdr2 = vmul(dr, vbc<V>(wf(7) * sc)), wr2 = vmul(rho, vbc<V>(wf(7) * sc));
+    const V wr13 = vmul(wr1, vbc<V>(3.0f)), wr23 = vmul(wr2, vbc<V>(3.0f));
+    V rest = vbc<V>(0.0f);
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const int qb = opp(q);
-        if (qb < q) continue;  // each pair once, from its lower member
+        if (qb < q) continue;  // each pair once
+        // p: the member whose leading nonzero velocity component is positive
+        const int p = (cx(q) > 0 || (cx(q) == 0 && (cy(q) > 0 || (cy(q) == 0 && cz(q) > 0)))) ? q : qb;
         const bool axis = q <= 6;
-        const float wdr = axis ? wdr1 : wdr2, wr = axis ? wr1 : wr2, wr3 = axis ? wr13 : wr23;
-        const float cu = (float)cx(q) * ux + (float)cy(q) * uy + (float)cz(q) * uz;
-        const float ca = (float)cx(q) * ax + (float)cy(q) * ay + (float)cz(q) * az;
-        const float A = wdr + wr * (4.5f * cu * cu - 1.5f * usq);
-        const float B = wr3 * cu;
-        const float C = wr * (9.0f * cu * ca) - wr * ua3;
-        const float D = wr3 * ca;
-        const float E = om * A + C, G = om * B + D;
-        const float dn = om1 * dp[q] + (E + G);
-        const float dnb = om1 * dp[qb] + (E - G);
-        rest += dp[q] - store(q, dn);
-        rest += dp[qb] - store(qb, dnb);
+        const V wdr = axis ? wdr1 : wdr2, wr = axis ? wr1 : wr2, wr3 = axis ? wr13 : wr23;
+        V cu = cx(p) ? ux : (cy(p) ? uy : uz);  // the leading component is +1
+        if (cx(p) && cy(p) > 0) cu = vadd(cu, uy);
+        if (cx(p) && cy(p) < 0) cu = vsub(cu, uy);
+        if ((cx(p) || cy(p)) && cz(p) > 0) cu = vadd(cu, uz);
+        if ((cx(p) || cy(p)) && cz(p) < 0) cu = vsub(cu, uz);
+        const float ca = (float)cx(p) * ax + (float)cy(p) * ay + (float)cz(p) * az;
+        const V A = vfma(wr, vfma(vmul(cu, cu), vbc<V>(4.5f), nusq15), wdr);
+        const V C = vmul(wr, vfma(cu, vbc<V>(9.0f * ca), nua3));
+        const V E = vfma(A, vbc<V>(om), C);
+        const V G = vfma(vmul(wr3, cu), vbc<V>(om), vmul(wr3, vbc<V>(ca)));
+        const V dnp = vfma(dp[p], vbc<V>(om1), vadd(E, G));
+        const int m = p == q ? qb : q;
+        const V dnm = vfma(dp[m], vbc<V>(om1), vsub(E, G));
+        rest = vadd(rest, vsub(dp[p], store(p, dnp)));
+        rest = vadd(rest, vsub(dp[m], store(m, dnm)));
     }
-    store(0, dp[0] + rest * isc);
+    store(0, vfma(rest, vbc<V>(isc), dp[0]));
     return rho;
 }
 
@@ -835,6 +898,30 @@ __device__ __forceinline__ long long fixed_point(float v, int s) {
     return (b >> 31) ? -r : r;
 }
 
+// Double-precision sums of Eqs. netforce and torque, exact and independent of
+// the order of the terms: a term t (|t| < 2^31) becomes the integer
+// floor(t 2^96) (its bits below 2^-96 dropped) and the integers are added in
+// 128-bit two's complement; the total v = H 2^64 + L (H signed, L unsigned)
+// becomes the double H 2^-32 + L 2^-96.  The plain CPU restatement sums the
+// same way, so both give the same bits whatever the thread order.
+__device__ __forceinline__ unsigned __int128 fixed96(double t) {
+    const double sc = t * 4294967296.0;  // t 2^32, exact
+    const double hf = floor(sc);
+    const long long hi = (long long)hf;
+    const unsigned long long lo = (unsigned long long)((sc - hf) * 18446744073709551616.0);
+    return ((unsigned __int128)(unsigned long long)hi << 64) | (unsigned __int128)lo;
+}
+__device__ __forceinline__ double fixed96_value(unsigned __int128 v) {
+    const long long H = (long long)(unsigned long long)(v >> 64);
+    const unsigned long long L = (unsigned long long)v;
+    return (double)H * 2.3283064365386962890625e-10 + (double)L * 1.2621774483536188886587657044524580e-29;
+}
+__device__ __forceinline__ unsigned __int128 shfl_down_128(unsigned __int128 v, int off) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, off);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(v >> 64), off);
+    return ((unsigned __int128)hi << 64) | (unsigned __int128)lo;
+}
+
 template <int S>
 __device__ __forceinline__ void forces_f64_body(const Dev &d, const VB &vb) {
     int bi = vb.y;
@@ -850,10 +937,9 @@ __device__ __forceinline__ void forces_f64_body(const Dev &d, const VB &vb) {
             hi[k] = lo[k] + n3[k];
         }
     }
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    // the cells of the box around the body spread over all the body's blocks
-    // (a fixed cell-to-thread map: the sums below stay deterministic); only
-    // cells next to an obstacle (neighbour-obstacle bit) can hold links
+    unsigned __int128 acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    // the cells of the box around the body spread over all the body's blocks;
+    // only cells next to an obstacle (neighbour-obstacle bit) can hold links
     const long long ncell = range_count(lo, hi);
     const int tidf = threadIdx.x + blockDim.x * threadIdx.y, nthr = blockDim.x * blockDim.y;
     for (long long kk = (long long)vb.x * nthr + tidf; kk < ncell; kk += (long long)vb.nx * nthr) {
@@ -896,34 +982,38 @@ __device__ __forceinline__ void forces_f64_body(const Dev &d, const VB &vb) {
                 }
                 double g = 2.0 * inner;
                 double F0 = cx(qb) * g, F1 = cy(qb) * g, F2 = cz(qb) * g;
-                acc[0] += F0;
-                acc[1] += F1;
-                acc[2] += F2;
-                acc[3] += r[1] * F2 - r[2] * F1;
-                acc[4] += r[2] * F0 - r[0] * F2;
-                acc[5] += r[0] * F1 - r[1] * F0;
-                acc[6] += fabs(g);
+                acc[0] += fixed96(F0);
+                acc[1] += fixed96(F1);
+                acc[2] += fixed96(F2);
+                acc[3] += fixed96(r[1] * F2 - r[2] * F1);
+                acc[4] += fixed96(r[2] * F0 - r[0] * F2);
+                acc[5] += fixed96(r[0] * F1 - r[1] * F0);
+                acc[6] += fixed96(fabs(g));
             }
         }
     }
-    // deterministic block reduction (fixed shuffle tree, then warps in order);
-    // a warp without any link skips the tree (its sums are exact zeros)
-    __shared__ double sh[8][7];
+    // block reduction of the exact integer sums (any order gives the same
+    // bits); a warp without any link skips the tree (its sums are zeros).
+    // The block's partials go out as 128-bit integers (low, high word).
+    __shared__ unsigned __int128 sh[8][7];
     int tid = threadIdx.x + blockDim.x * threadIdx.y;
     int lane = tid & 31, wid = tid >> 5;
-    const bool any = __any_sync(0xffffffffu, acc[6] != 0.0 || acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0);
+    const bool any = __any_sync(0xffffffffu, (acc[6] | acc[0] | acc[1] | acc[2]) != 0);
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
-        double v = acc[c];
+        unsigned __int128 v = acc[c];
         if (any)
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            for (int off = 16; off > 0; off >>= 1) v += shfl_down_128(v, off);
         if (lane == 0) sh[wid][c] = v;
     }
     __syncthreads();
     if (tid < 7) {
-        double v = 0.0;
+        unsigned __int128 v = 0;
         for (int w = 0; w < 8; ++w) v += sh[w][tid];
-        d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = v;
+        unsigned long long *p = reinterpret_cast<unsigned long long *>(d.part) +
+                                2 * (((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid);
+        p[0] = (unsigned long long)v;
+        p[1] = (unsigned long long)(v >> 64);
     }
 }
 
@@ -1187,10 +1277,10 @@ __device__ __noinline__ Bounce<typename Sto<S>::R> bounce_back(const Dev &d, int
 
 // ---- C1 + C2 for liquid cells (Sec. 2.1 Eqs. stream, lbgk, forceterm;
 // Sec. 2.3 Eq. noslip); interface cells are listed for k_interface
-template <int S>
-__device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z);
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int y, int z0, int z1);
+template <int S, int ZBMAX>
+__device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int zb);
 
 // A block covers BULK_THREADS consecutive cells of an xy-plane (row ends
 // wrap to the next row, so narrow grids keep every lane busy) for zb
@@ -1207,9 +1297,15 @@ __device__ __forceinline__ void liquid_body(const Dev &d, const VB &vb, int zb) 
     const int z1 = min(z0 + zb, d.nz);
     liquid_column<S, ZBMAX>(d, in, x, y, z0, z1);
 }
+// the bulk body of a storage: one cell per thread (double), two (float)
+template <int S, int ZBMAX>
+__device__ __forceinline__ void bulk_body(const Dev &d, const VB &vb, int zb) {
+    if constexpr (S == 0) liquid_body<S, ZBMAX>(d, vb, zb);
+    else liquid_body_pair<S, ZBMAX>(d, vb, zb);
+}
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB) k_liquid(const __grid_constant__ Dev d) {
-    liquid_body<S, LBMFS_BULK_ZB>(d, vb_own(), LBMFS_BULK_ZB);
+__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_PAIR_MINB) k_liquid(const __grid_constant__ Dev d) {
+    bulk_body<S, LBMFS_BULK_ZB>(d, vb_own(), LBMFS_BULK_ZB);
 }
 
 template <int S>
@@ -1229,8 +1325,8 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         // fp in the storage's raw units (to_raw)
         void *g = d.fdst;
         const long long N = d.N;
-        float rho = collide_store_f<P::SCALE>(d, fp, [&](int q, float v) { return P::st_raw(g, q, i, N, v); });
-        if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+        float rho = collide_store_v<P::SCALE, float>(d, fp, [&](int q, float v) { return P::st_raw(g, q, i, N, v); });
+        if (!vpos_finite(rho)) atomicOr(d.status, ST_NONFINITE);
     }
 }
 
@@ -1275,30 +1371,47 @@ __device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, 
     collide_store<S>(d, fp, i);
 }
 
+// One liquid cell (class byte c, coordinates x, y, z, index i): gather its
+// 18 arriving populations by the cheapest rule that holds for it, collide and
+// store.
 template <int S>
-__device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
+__device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, int z, long long i) {
     using P = Sto<S>;
     using R = typename P::R;
-    bool in = x < d.nx;
-    long long i = (long long)(in ? x : 0) + (long long)d.nx * (y + (long long)d.ny * z);
-    int c = in ? (int)d.flags[i] : 0;
-    wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
-    if ((c & CL_MASK) != CL_L) return;
-    const bool interior = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
     R fp[Q];
-    if (c == CL_L && interior) {
+    if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
         // no obstacle or wall in the neighbourhood and a liquid cell never
-        // touches gas: plain pull from the 18 neighbours, no flag loads
-        const long long N = d.N;
-        const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
+        // touches gas: plain pull from the 18 neighbours
 #pragma unroll
-        for (int q = 1; q < Q; ++q) fp[q] = P::ld_raw(d.fsrc, q, i - (cx(q) * sx + cy(q) * sy + cz(q) * sz), N);
-        fp[0] = P::ld_raw(d.fsrc, 0, i, N);
+        for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+        fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
+    } else if (c == CL_L && !d.periodic && !d.walls_move) {
+        // on a face of a grid without periodic axes, no obstacle
+        // neighbour: a source beyond a face is a resting wall, which
+        // returns the cell's own opposite population (Eq. noslip, u_w = 0)
+        const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0, zh = z == d.nz - 1;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
+                             (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
+            fp[q] = out ? P::ldg_raw(d.fsrc, opp(q), i, N)
+                        : P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+        }
+        fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
+    } else if (c == CL_L && !d.walls_move) {
+        // on a face with periodic axes: pull across the seams, walls as above
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            fp[q] = si >= 0 ? P::ldg_raw(d.fsrc, q, si, N) : P::ldg_raw(d.fsrc, opp(q), i, N);
+        }
+        fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
     } else {
         gather_general<S>(d, x, y, z, i, fp);
         to_raw<S>(fp);
     }
-    collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
+    collide_store<S>(d, fp, i);
 }
 
 // The cells (x, y, z0 .. z1-1) of one thread.  The flags of the whole column
@@ -1306,12 +1419,9 @@ __device__ __forceinline__ void liquid_cell(const Dev &d, int x, int y, int z) {
 // after one memory latency, and a fluid cell waits on its populations only.
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int y, int z0, int z1) {
-    using P = Sto<S>;
-    using R = typename P::R;
     static_assert(ZBMAX <= 8, "flags of a column (z1 - z0 <= ZBMAX) are packed into 64 bits");
-    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     long long i = (long long)x + sy * (y + (long long)d.ny * z0);
-    const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1;
     uint64_t fl = 0;
 #pragma unroll
     for (int k = 0; k < ZBMAX; ++k)
@@ -1326,40 +1436,75 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
         fl >>= 8;
         wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
         if ((c & CL_MASK) != CL_L) continue;
-        R fp[Q];
-        if (c == CL_L && inner && z > 0 && z < d.nz - 1) {
-            // no obstacle or wall in the neighbourhood and a liquid cell never
-            // touches gas: plain pull from the 18 neighbours
+        liquid_one<S>(d, c, x, y, z, i);  // one copy of the collision in the kernel
+    }
+}
+
+// Float storages: two cells per thread, the cells p = 2t and 2t + 1 of the
+// xy-plane in linear order (a block covers 2 BULK_THREADS of them), zb
+// z-planes.  Where both are interior liquid cells with no obstacle or wall
+// among their neighbours -- almost every liquid cell -- each direction's two
+// arriving populations come in one load (two when the pair's source starts on
+// an odd element: the +-x directions, odd row or plane strides) and the two
+// cells collide together in packed FP32 arithmetic (float2 operations, the
+// same roundings per cell as the single-cell path), storing each direction's
+// pair with one store.  That halves the load, store and arithmetic
+// instructions per cell.  Every other cell takes the single-cell path.
+template <int S, int ZBMAX>
+__device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int zb) {
+    using P = Sto<S>;
+    static_assert(S != 0, "pairs serve the float storages");
+    if ((int)(vb.z * zb) > __ldg(d.ztop_rd) + ZTOP_MARGIN) return;
+    const unsigned nxy = (unsigned)d.nx * (unsigned)d.ny;
+    const unsigned p0 = 2u * (vb.x * BULK_THREADS + threadIdx.x);
+    const bool in0 = p0 < nxy, in1 = p0 + 1u < nxy;
+    const int y0 = in0 ? (int)(p0 / (unsigned)d.nx) : 0;
+    const int x0 = in0 ? (int)p0 - y0 * d.nx : 0;
+    const int x1 = x0 + 1 == d.nx ? 0 : x0 + 1, y1 = x0 + 1 == d.nx ? y0 + 1 : y0;
+    const int z0 = vb.z * zb, z1 = min(z0 + zb, d.nz);
+    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
+    long long i = (long long)p0 + sz * z0;  // cell 0 at z; cell 1 is i + 1
+    // classes of both columns in one round of loads: cell 0 in the low byte
+    unsigned fl[ZBMAX];
+    unsigned any = 0;
 #pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
-            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-        } else if (c == CL_L && !d.periodic && !d.walls_move) {
-            // on a face of a grid without periodic axes, no obstacle
-            // neighbour: a source beyond a face is a resting wall, which
-            // returns the cell's own opposite population (Eq. noslip, u_w = 0)
-            const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0,
-                       zh = z == d.nz - 1;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
-                                 (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
-                fp[q] = out ? P::ldg_raw(d.fsrc, opp(q), i, N)
-                            : P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
-            }
-            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-        } else if (c == CL_L && !d.walls_move) {
-            // on a face with periodic axes: pull across the seams, walls as above
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                fp[q] = si >= 0 ? P::ldg_raw(d.fsrc, q, si, N) : P::ldg_raw(d.fsrc, opp(q), i, N);
-            }
-            fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-        } else {
-            gather_general<S>(d, x, y, z, i, fp);
-            to_raw<S>(fp);
+    for (int k = 0; k < ZBMAX; ++k) {
+        const long long j = i + k * sz;
+        unsigned v = 0;
+        if (in0 && z0 + k < z1) {
+            if (in1 && !(j & 1)) v = *reinterpret_cast<const uint16_t *>(d.flags + j);
+            else v = (unsigned)d.flags[j] | (in1 ? (unsigned)d.flags[j + 1] << 8 : 0u);
         }
-        collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
+        fl[k] = v;
+        any |= v;
+    }
+    if (__any_sync(0xffffffffu, (any & 0x0303u) != 0) && (threadIdx.x & 31) == 0) atomicMax(d.ztop_wr, z1 - 1);
+    if (any == 0) return;
+    const bool pair_xy = in1 && y1 == y0 && x0 > 0 && x1 < d.nx - 1 && y0 > 0 && y0 < d.ny - 1;
+#pragma unroll 1
+    for (int k = 0; k < ZBMAX; ++k, i += sz) {
+        const int z = z0 + k;
+        if (z >= z1) break;
+        const int c0 = (int)(fl[k] & 0xffu), c1 = (int)(fl[k] >> 8);
+        wl_append(d, (c0 & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
+        wl_append(d, (c1 & CL_MASK) == CL_I, WL_IFACE, (uint32_t)(i + 1));
+        if (pair_xy && c0 == CL_L && c1 == CL_L && z > 0 && z < d.nz - 1) {
+            float2 fp[Q];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) fp[q] = P::ldg_pair_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
+            fp[0] = P::ldg_pair_raw(d.fsrc, 0, i, N);
+            void *g = d.fdst;
+            const float2 rho = collide_store_v<P::SCALE, float2>(
+                d, fp, [&](int q, float2 v) { return P::st_pair_raw(g, q, i, N, v); });
+            if (!vpos_finite(rho)) atomicOr(d.status, ST_NONFINITE);
+        } else {
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int c = h ? c1 : c0;
+                if ((c & CL_MASK) != CL_L) continue;
+                liquid_one<S>(d, c, h ? x1 : x0, h ? y1 : y0, z, i + h);
+            }
+        }
     }
 }
 
@@ -1891,7 +2036,7 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             m_new = d.m[i] + (double)dm;
             void *g = d.fdst;
             float drs = 0.0f;
-            float rho = collide_store_f(d, fp, [&](int q, float v) {
+            float rho = collide_store_v<1, float>(d, fp, [&](int q, float v) {
                 float st = P::st_one(g, q, i, N, v);
                 drs += st;
                 return st;
@@ -2193,12 +2338,27 @@ __device__ __forceinline__ void bodies_body(const Dev &d, const VB &vb) {
     int bi = vb.x;
     int lane = threadIdx.x;
     double acc[7];
+    if (d.part128) {
+        // double storage: exact 128-bit partials (fixed96), summed exactly
+        const unsigned long long *pp = reinterpret_cast<const unsigned long long *>(d.part);
+#pragma unroll 1
+        for (int c = 0; c < 7; ++c) {
+            unsigned __int128 v = 0;
+            for (int k = lane; k < FORCE_BLOCKS; k += 32) {
+                const long long j = 2 * (((long long)bi * FORCE_BLOCKS + k) * 7 + c);
+                v += ((unsigned __int128)pp[j + 1] << 64) | (unsigned __int128)pp[j];
+            }
+            for (int off = 16; off > 0; off >>= 1) v += shfl_down_128(v, off);
+            acc[c] = fixed96_value(v);
+        }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-        double v = 0.0;
-        for (int k = lane; k < FORCE_BLOCKS; k += 32) v += d.part[((long long)bi * FORCE_BLOCKS + k) * 7 + c];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        acc[c] = v;
+        for (int c = 0; c < 7; ++c) {
+            double v = 0.0;
+            for (int k = lane; k < FORCE_BLOCKS; k += 32) v += d.part[((long long)bi * FORCE_BLOCKS + k) * 7 + c];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            acc[c] = v;
+        }
     }
     if (lane != 0) return;
     // the body record is read once into registers, updated, and written back
@@ -2586,7 +2746,7 @@ struct BkReset {
 template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, true, forces_body<S>(d, vb))
 // one instantiation per z-planes-per-tile choice (the column loop unrolled to it)
 template <int S, int ZB>
-LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_BULK_MINB, (liquid_body<S, ZB>(d, vb, zb)))
+LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_PAIR_MINB, (bulk_body<S, ZB>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
@@ -2654,7 +2814,7 @@ template <int S> struct Launch {
         mark();
         {
             const long long nxy = (long long)d.nx * d.ny;
-            dim3 grid((unsigned)((nxy + BULK_THREADS - 1) / BULK_THREADS), 1, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
+            dim3 grid((unsigned)((nxy + BULK_CELLS[S] - 1) / BULK_CELLS[S]), 1, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
             if constexpr (S != 0) {
                 // the staged variants tile rows: (ceil(nx / BULK_THREADS), ny, z-blocks)
                 dim3 rgrid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
@@ -2773,6 +2933,7 @@ template <int S> KernelSet make_kernel_set() {
     k.bulk_blocks_per_sm = &BatchStep<S>::bulk_blocks_per_sm;
     k.nkernels = 16;
     k.names = kernel_names();
+    k.bulk_cells = BULK_CELLS[S];
     return k;
 }
 

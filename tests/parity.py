@@ -57,3 +57,42 @@ def macro_errors(g, o):
     du = np.linalg.norm(g["u"][same] - o["u"][same], axis=1).max()
     return dict(rho=float(drho.max()), u=float(du / umax) if umax > 0 else float(du), u_abs=float(du),
                 u_max=float(umax), flag_diff=int((g["flags"] != o["flags"]).sum()))
+
+
+# unit roundoff of one stored population deviation f_q - w_q: FP32, and the
+# 11-bit significand of the scaled half of the FP16-shifted storage
+UNIT_ROUNDOFF = {"f32": 2.0 ** -24, "f16s": 2.0 ** -11}
+# roundings of a population's size per step: the relaxation, the equilibrium
+# and force terms of the float collision, and the store
+ROUNDINGS_PER_STEP = 4
+
+
+def rounding_floor(o, storage, steps):
+    """Velocity that a float storage's rounding can leave after `steps` steps.
+    Each step rounds every stored deviation d_q = f_q - w_q (and the collision
+    terms of its size, ROUNDINGS_PER_STEP of them) to the storage's unit
+    roundoff u, which moves a cell's momentum sum_q c_qk d_q by up to
+    4 u V, V = the largest sum_q |c_qk| |d_q| over the oracle's fluid cells and
+    the three axes.  The roundings of successive steps are independent, so
+    they add like a random walk: 4 u V sqrt(steps)."""
+    import oracle
+
+    c, w, _ = oracle.lattice()
+    fluid = (o["flags"] == 1) | (o["flags"] == 2)
+    d = np.abs(o["f"][:, fluid] - w[:, None])
+    V = max(float((np.abs(c[:, k])[:, None] * d).sum(axis=0).max()) for k in range(3))
+    return ROUNDINGS_PER_STEP * UNIT_ROUNDOFF[storage] * V * float(np.sqrt(steps))
+
+
+def velocity_check(g, o, storage, tol, steps):
+    """Largest velocity errors over liquid and over interface cells whose class
+    agrees, and the bound both must meet: tol times the largest oracle speed
+    plus the rounding floor."""
+    same = g["flags"] == o["flags"]
+    fluid = same & ((o["flags"] == 1) | (o["flags"] == 2))
+    umax = float(np.linalg.norm(o["u"][fluid], axis=1).max())
+    du = np.linalg.norm(g["u"] - o["u"], axis=1)
+    e_liq = float(du[same & (o["flags"] == 1)].max()) if (same & (o["flags"] == 1)).any() else 0.0
+    e_if = float(du[same & (o["flags"] == 2)].max()) if (same & (o["flags"] == 2)).any() else 0.0
+    bound = tol * umax + rounding_floor(o, storage, steps)
+    return e_liq, e_if, bound, umax

@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_1201_0351_gb300 import inputs as I
 
-from parity import assert_f64_parity, macro_errors
+from parity import assert_f64_parity, macro_errors, velocity_check
 
 pytestmark = pytest.mark.gpu
 
@@ -94,16 +94,20 @@ def test_batch_f64_matches_oracle():
 
 def test_batch_f16s_against_oracle():
     """FP16-shifted storage in the batch (the sweep's storage) against the
-    FP64 oracle: density within 2e-3, classes identical."""
+    FP64 oracle: density within 2e-3, classes identical, velocity within 2e-3
+    of the largest speed plus the rounding floor, torque within 2e-3 of its
+    scale."""
     scenes = sorted(I.batched_sweep_tanks(64), key=lambda s: s.nx)[:3]
     steps = 60
     res, _ = _batched(scenes, "f16s", steps)
     for sc, (g, gb, gs) in zip(scenes, res):
         ref = oracle.OracleSim(sc)
         ref.step(steps)
-        o = ref.fields()
+        o = ref.fields(want_f=True)
         e = macro_errors(g, o)
         assert e["flag_diff"] == 0 and e["rho"] <= 2e-3, (sc.name, e)
+        e_liq, e_if, bound, umax = velocity_check(g, o, "f16s", 2e-3, steps)
+        assert e_liq <= bound and e_if <= bound, (sc.name, e_liq, e_if, bound)
         ob = ref.body(0)
         lever = float(np.linalg.norm(sc.boxes[0].half))  # torque scale: force scale x half diagonal
         assert abs(gb[0]["T"][0] - ob["T"][0]) <= 2e-3 * gb[0]["S"] * lever, (gb[0]["T"], ob["T"])

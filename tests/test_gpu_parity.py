@@ -12,7 +12,7 @@ import pytest
 
 from paper_1201_0351_gb300 import inputs as I
 
-from parity import assert_f64_parity, macro_errors, run_both
+from parity import assert_f64_parity, macro_errors, run_both, velocity_check
 
 pytestmark = pytest.mark.gpu
 
@@ -106,12 +106,16 @@ def test_graph_and_stream_launch_agree():
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16s", 2e-3)])
 def test_reduced_precision_closed_tank(storage, tol):
     """FP32 / FP16-shifted storage against the FP64 oracle after 200 steps of
-    the closed tank with the fixed box: density relative error and buoyancy."""
+    the closed tank with the fixed box: density relative error, buoyancy, and
+    velocity within tol of the largest oracle speed plus the storage's
+    rounding floor (at rest the speeds are ~1e-5, near that floor)."""
     g, o, gb, ob, gs, ref = run_both(I.closed_tank_32(), 200, storage=storage)
     e = macro_errors(g, o)
-    print(storage, e)
+    e_liq, e_if, bound, umax = velocity_check(g, o, storage, tol, 200)
+    print(storage, e, "liquid", e_liq, "interface", e_if, "bound", bound)
     assert e["flag_diff"] == 0, e
     assert e["rho"] <= tol, e
+    assert e_liq <= bound and e_if <= bound, (e_liq, e_if, bound)
     fz = ob[0]["F"][2]
     assert abs(gb[0]["F"][2] - fz) <= tol * gb[0]["S"], (gb[0]["F"], ob[0]["F"])
 
@@ -119,19 +123,14 @@ def test_reduced_precision_closed_tank(storage, tol):
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16s", 2e-3)])
 def test_reduced_precision_channel_velocity(storage, tol):
     """Body-force driven channel with the free box, after 200 steps: density
-    error and velocity error relative to the largest oracle speed, over liquid
-    cells; interface cells (whose velocity comes from reconstructed
-    populations and carries the storage's quantisation noise without the
-    averaging of a full stencil) are held to five times the tolerance."""
+    error, and the velocity error of liquid and interface cells within tol of
+    the largest oracle speed plus the storage's rounding floor."""
     g, o, gb, ob, gs, ref = run_both(I.channel_96x32x32(), 200, storage=storage)
     e = macro_errors(g, o)
-    same = g["flags"] == o["flags"]
-    umax = np.linalg.norm(o["u"], axis=1).max()
-    du = np.linalg.norm(g["u"] - o["u"], axis=1) / umax
-    e_liq = du[same & (o["flags"] == I.LIQUID)].max()
-    e_if = du[same & (o["flags"] == I.INTERFACE)].max()
-    print(storage, e, "liquid", e_liq, "interface", e_if)
-    assert e["rho"] <= tol and e_liq <= tol and e_if <= 5 * tol, (e, e_liq, e_if)
+    e_liq, e_if, bound, umax = velocity_check(g, o, storage, tol, 200)
+    print(storage, e, "liquid", e_liq, "interface", e_if, "bound", bound, "tol*umax", tol * umax)
+    assert e["flag_diff"] == 0 and e["rho"] <= tol, e
+    assert e_liq <= bound and e_if <= bound, (e_liq, e_if, bound)
 
 
 def test_mass_ledger_identity_f64():
@@ -239,7 +238,8 @@ def test_reduced_precision_box_across_periodic_seams(storage, tol):
     """A moving, rotated box whose cell range wraps around the periodic seams
     on every axis (the float force kernel maps the wrapped rows to threads):
     after 120 steps its force and torque match the oracle within the storage's
-    tolerance of the link-term sum S, and the fluid within the same bound."""
+    tolerance of the link-term sum S, the density within the tolerance and the
+    velocity within tol of the largest speed plus the rounding floor."""
     n = 16
     u0 = np.array([6e-3, -2.5e-3, 1.5e-3])
     fl, fi, rh = I.uniform_state(n, n, n, I.LIQUID)
@@ -249,7 +249,9 @@ def test_reduced_precision_box_across_periodic_seams(storage, tol):
                     [box], 0, np.tile(u0, n ** 3))
     g, o, gb, ob, gs, _ = run_both(sc, 120, storage=storage)
     e = macro_errors(g, o)
+    e_liq, e_if, bound, umax = velocity_check(g, o, storage, tol, 120)
+    print(storage, e, "liquid", e_liq, "bound", bound, "tol*umax", tol * umax)
     assert e["flag_diff"] == 0, e
-    assert e["rho"] <= tol and e["u"] <= 10 * tol, e
+    assert e["rho"] <= tol and e_liq <= bound and e_if <= bound, (e, e_liq, e_if, bound)
     for key in ("F", "T"):
         assert np.abs(np.asarray(gb[0][key]) - np.asarray(ob[0][key])).max() <= tol * ob[0]["S"], (key, gb[0], ob[0])

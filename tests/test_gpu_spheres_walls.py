@@ -9,7 +9,7 @@ import pytest
 
 from paper_1201_0351_gb300 import inputs as I
 
-from parity import assert_f64_parity, macro_errors, run_both
+from parity import assert_f64_parity, macro_errors, run_both, velocity_check
 
 pytestmark = pytest.mark.gpu
 
@@ -35,14 +35,17 @@ def test_f64_parity_spheres_and_moving_walls(make, steps):
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16s", 2e-3)])
 def test_reduced_precision_free_advection(storage, tol):
+    """The sphere is carried by the liquid around it: its velocity is held to
+    the same bound as the liquid's (tol of the largest speed plus the
+    storage's rounding floor)."""
     g, o, gb, ob, gs, ref = run_both(_small_channel(), 150, storage=storage)
     e = macro_errors(g, o)
     assert e["flag_diff"] == 0 and e["rho"] <= tol, e
-    umax = np.linalg.norm(o["u"], axis=1).max()
-    liquid = o["flags"] == I.LIQUID
-    du = np.linalg.norm(g["u"] - o["u"], axis=1)[liquid].max()
-    assert du <= tol * umax, (du, umax)
-    assert abs(gb[0]["vel"][0] - ob[0]["vel"][0]) <= 10 * tol * 2e-3, (gb[0]["vel"], ob[0]["vel"])
+    e_liq, e_if, bound, umax = velocity_check(g, o, storage, tol, 150)
+    dv = float(np.abs(gb[0]["vel"] - ob[0]["vel"]).max())
+    print(storage, "liquid", e_liq, "interface", e_if, "sphere", dv, "bound", bound, "tol*umax", tol * umax)
+    assert e_liq <= bound and e_if <= bound, (e_liq, e_if, bound)
+    assert dv <= bound, (gb[0]["vel"], ob[0]["vel"], bound)
 
 
 @pytest.mark.parametrize("tau,bound", [(1.1, 0.05), (0.8, 0.10)])
