@@ -126,6 +126,9 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return fail(LBM_FS_EINVAL, "grid sizes must be positive%s");
     long long N = (long long)p->nx * p->ny * p->nz;
     if (N >= 0xFFFFFFFFll) return fail(LBM_FS_EINVAL, "grid has 2^32 cells or more%s");
+    // the float storages' bulk kernel indexes a population as q N + cell in 32 bits
+    if (p->storage != LBM_FS_F64 && N * Q >= 0xFFFFFFFFll)
+        return fail(LBM_FS_EINVAL, "float storages take fewer than 2^32 / 19 cells%s");
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBM_FS_EINVAL, "tau must exceed 1/2%s");
     if (p->storage < LBM_FS_F64 || p->storage > LBM_FS_F16S) return fail(LBM_FS_EINVAL, "unknown storage%s");
     if (!p->init_flags || !p->init_fill || !p->init_rho) return fail(LBM_FS_EINVAL, "init_flags, init_fill and init_rho are required%s");
@@ -194,6 +197,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.vmass = rd_vm ? p->virtual_mass : 1.0;
     d.force_mean = (p->readings & LBM_FS_READING_FORCE_MEAN) ? (p->force_mean != 0) : 1;
     d.nb_rule = (p->readings & LBM_FS_READING_NEIGHBOUR_RULE) ? (p->neighbour_rule != 0) : 1;
+    d.pair_ok = p->storage != LBM_FS_F64 && p->nx % 2 == 0 && N % 2 == 0;
     // row segments are 16-byte aligned when nx is a multiple of 16 / element size
     // bulk-kernel variant (float storages): direct loads by default;
     // LBMFS_BULK=pipe|tma selects the shared-memory staged variants (both

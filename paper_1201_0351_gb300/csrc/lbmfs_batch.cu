@@ -126,7 +126,7 @@ lbm_fs_status build(lbm_fs_batch *b) {
             tb[SH_TANK].push_back(tile(j, 0, 0, 0, 1, 1, 1));
             for (int y = 0; y < nb; ++y)
                 for (int x = 0; x < FORCE_BLOCKS; ++x) tb[SH_FORCE].push_back(tile(j, x, y, 0, FORCE_BLOCKS, nb, 1));
-            const int bc = b->tanks[0]->ks.bulk_cells;
+            const int bc = bulk_cells(t->p.storage, d);
             const int gx = (int)(((long long)d.nx * d.ny + bc - 1) / bc);
             const int gz = (d.nz + b->zb - 1) / b->zb;
             for (int z = 0; z < gz; ++z)

@@ -22,7 +22,9 @@ constexpr int GRID_GUARD = 1024;
 constexpr int BULK_THREADS = LBMFS_BULK_THREADS;  // x extent of a bulk-kernel block
 // cells of an xy-plane per bulk-kernel block, by storage: one per thread for
 // double, two per thread for the float storages
-constexpr int BULK_CELLS[3] = {BULK_THREADS, 2 * BULK_THREADS, 2 * BULK_THREADS};
+#ifndef LBMFS_BULK_PAIR
+#define LBMFS_BULK_PAIR 1  // float storages on even grids: two cells per bulk-kernel thread
+#endif
 
 // cell classes (as in the C ABI) in the low nibble of the flag byte; bit 4
 // marks a cell with an obstacle or a wall among its 18 neighbours
@@ -92,6 +94,7 @@ struct Dev {
     double vmass;      // virtual-mass coefficient of the rigid-body update
     int force_mean;    // rigid-body update driven by (F_n + F_{n-1}) / 2
     int nb_rule;       // interface cells without liquid (gas) neighbours empty (fill)
+    int pair_ok;       // nx and N even: the float bulk kernel takes two cells per thread
 };
 
 // bulk-kernel variants: direct loads, per-thread cp.async pipeline over z,
@@ -153,8 +156,13 @@ struct KernelSet {
     int (*bulk_blocks_per_sm)();
     int nkernels;
     const char *const *names;
-    int bulk_cells;  // cells of an xy-plane per bulk-kernel block
 };
+
+// cells of an xy-plane per bulk-kernel block: two per thread for the float
+// storages on grids with nx and the cell count even, one otherwise
+inline int bulk_cells(int storage, const Dev &d) {
+    return (storage != 0 && LBMFS_BULK_PAIR && d.pair_ok) ? 2 * BULK_THREADS : BULK_THREADS;
+}
 
 // The rigid-body update (double precision, independent of the storage) is
 // compiled once, in the unit built without fused multiply-add, and launched

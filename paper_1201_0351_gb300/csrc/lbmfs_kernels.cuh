@@ -62,6 +62,9 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 #ifndef LBMFS_BULK_MINB
 #define LBMFS_BULK_MINB 8  // resident blocks per SM asked of ptxas for the bulk kernel (64 registers)
 #endif
+#ifndef LBMFS_BULK_PAIR
+#define LBMFS_BULK_PAIR 1  // float storages: two cells per bulk-kernel thread
+#endif
 #ifndef LBMFS_PAIR_MINB
 #define LBMFS_PAIR_MINB 5  // resident blocks per SM of the two-cell bulk kernel (float storages, 96 registers)
 #endif
@@ -310,6 +313,81 @@ template <> struct Sto<2> {
             pop_st(reinterpret_cast<__half2 *>(h), hv);
         }
         return __half22float2(hv);
+    }
+};
+
+// The bulk kernel's view of one population grid: 32-bit element indices
+// (q N + j < 2^32 for the float storages, checked at create) from one base
+// pointer per kind of plane, so an access costs one index multiply-add and
+// one widening address computation instead of 64-bit index arithmetic.
+template <int S> struct Planes;
+template <> struct Planes<1> {
+    const float *r;
+    float *w;
+    uint32_t N;
+    __device__ __forceinline__ Planes(const void *src, void *dst, long long n)
+        : r(reinterpret_cast<const float *>(src)), w(reinterpret_cast<float *>(dst)), N((uint32_t)n) {}
+    __device__ __forceinline__ float ld(int q, uint32_t j) const { return pop_ldg(r + ((uint32_t)q * N + j)); }
+    __device__ __forceinline__ float st(int q, uint32_t j, float v) const {
+        pop_st(w + ((uint32_t)q * N + j), v);
+        return v;
+    }
+    // the pair j, j + 1 when j + q N is even (one 8-byte load / store)
+    __device__ __forceinline__ float2 ld2(int q, uint32_t j) const {
+        return pop_ldg(reinterpret_cast<const float2 *>(r + ((uint32_t)q * N + j)));
+    }
+    // the pair j, j + 1 when j + q N is odd (two loads)
+    __device__ __forceinline__ float2 ld2_odd(int q, uint32_t j) const {
+        const float *b = r + ((uint32_t)q * N + j);
+        return make_float2(pop_ldg(b), pop_ldg(b + 1));
+    }
+    __device__ __forceinline__ float2 st2(int q, uint32_t j, float2 v) const {
+        pop_st(reinterpret_cast<float2 *>(w + ((uint32_t)q * N + j)), v);
+        return v;
+    }
+};
+template <> struct Planes<2> {
+    const float *r0;
+    const __half *rh;
+    float *w0;
+    __half *wh;
+    uint32_t N;
+    __device__ __forceinline__ Planes(const void *src, void *dst, long long n)
+        : r0(reinterpret_cast<const float *>(src)), rh(reinterpret_cast<const __half *>(r0 + n)),
+          w0(reinterpret_cast<float *>(dst)), wh(reinterpret_cast<__half *>(w0 + n)), N((uint32_t)n) {}
+    // raw units: q >= 1 times the storage's scale, the rest population unscaled
+    __device__ __forceinline__ float ld(int q, uint32_t j) const {
+        if (q == 0) return pop_ldg(r0 + j);
+        return __half2float(pop_ldg(rh + ((uint32_t)(q - 1) * N + j)));
+    }
+    __device__ __forceinline__ float st(int q, uint32_t j, float v) const {
+        if (q == 0) {
+            pop_st(w0 + j, v);
+            return v;
+        }
+        const __half h = __float2half_rn(v);
+        pop_st(wh + ((uint32_t)(q - 1) * N + j), h);
+        return __half2float(h);
+    }
+    __device__ __forceinline__ float2 ld2(int q, uint32_t j) const {
+        if (q == 0) return pop_ldg(reinterpret_cast<const float2 *>(r0 + j));
+        return __half22float2(pop_ldg(reinterpret_cast<const __half2 *>(rh + ((uint32_t)(q - 1) * N + j))));
+    }
+    __device__ __forceinline__ float2 ld2_odd(int q, uint32_t j) const {
+        if (q == 0) return make_float2(pop_ldg(r0 + j), pop_ldg(r0 + j + 1));
+        const __half *h = rh + ((uint32_t)(q - 1) * N + j);
+        const __half2 a = pop_ldg(reinterpret_cast<const __half2 *>(h - 1));
+        const __half2 b = pop_ldg(reinterpret_cast<const __half2 *>(h + 1));
+        return make_float2(__high2float(a), __low2float(b));
+    }
+    __device__ __forceinline__ float2 st2(int q, uint32_t j, float2 v) const {
+        if (q == 0) {
+            pop_st(reinterpret_cast<float2 *>(w0 + j), v);
+            return v;
+        }
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        pop_st(reinterpret_cast<__half2 *>(wh + ((uint32_t)(q - 1) * N + j)), h);
+        return __half22float2(h);
     }
 };
 
@@ -588,9 +666,20 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+#ifndef LBMFS_NO_F32X2
+#define LBMFS_NO_F32X2 0  // tuning knob: the pair's arithmetic as two scalar operations
+#endif
+#if LBMFS_NO_F32X2
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+#else
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#endif
 __device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
 template <class V> __device__ __forceinline__ V vbc(float s);
 template <> __device__ __forceinline__ float vbc<float>(float s) { return s; }
@@ -1300,8 +1389,9 @@ __device__ __forceinline__ void liquid_body(const Dev &d, const VB &vb, int zb) 
 // the bulk body of a storage: one cell per thread (double), two (float)
 template <int S, int ZBMAX>
 __device__ __forceinline__ void bulk_body(const Dev &d, const VB &vb, int zb) {
-    if constexpr (S == 0) liquid_body<S, ZBMAX>(d, vb, zb);
-    else liquid_body_pair<S, ZBMAX>(d, vb, zb);
+    if constexpr (S == 0 || !LBMFS_BULK_PAIR) liquid_body<S, ZBMAX>(d, vb, zb);
+    else if (d.pair_ok) liquid_body_pair<S, ZBMAX>(d, vb, zb);
+    else liquid_body<S, ZBMAX>(d, vb, zb);
 }
 template <int S>
 __global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_PAIR_MINB) k_liquid(const __grid_constant__ Dev d) {
@@ -1323,9 +1413,9 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
     } else {
         // fp in the storage's raw units (to_raw)
-        void *g = d.fdst;
-        const long long N = d.N;
-        float rho = collide_store_v<P::SCALE, float>(d, fp, [&](int q, float v) { return P::st_raw(g, q, i, N, v); });
+        const Planes<S> pl(d.fsrc, d.fdst, d.N);
+        const uint32_t j = (uint32_t)i;
+        float rho = collide_store_v<P::SCALE, float>(d, fp, [&](int q, float v) { return pl.st(q, j, v); });
         if (!vpos_finite(rho)) atomicOr(d.status, ST_NONFINITE);
     }
 }
@@ -1378,18 +1468,46 @@ template <int S>
 __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, int z, long long i) {
     using P = Sto<S>;
     using R = typename P::R;
-    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
+    const long long N = d.N;
     R fp[Q];
-    if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-        // no obstacle or wall in the neighbourhood and a liquid cell never
-        // touches gas: plain pull from the 18 neighbours
+    if constexpr (S != 0) {
+        const Planes<S> pl(d.fsrc, d.fdst, N);
+        const uint32_t j = (uint32_t)i, sy = (uint32_t)d.nx, sz = (uint32_t)d.nx * (uint32_t)d.ny;
+        if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+            // no obstacle or wall in the neighbourhood and a liquid cell never
+            // touches gas: plain pull from the 18 neighbours
+#pragma unroll
+            for (int q = 1; q < Q; ++q) fp[q] = pl.ld(q, j - (uint32_t)cx(q) - (uint32_t)cy(q) * sy - (uint32_t)cz(q) * sz);
+            fp[0] = pl.ld(0, j);
+            collide_store<S>(d, fp, i);
+            return;
+        }
+        if (c == CL_L && !d.periodic && !d.walls_move) {
+            // on a face of a grid without periodic axes, no obstacle
+            // neighbour: a source beyond a face is a resting wall, which
+            // returns the cell's own opposite population (Eq. noslip, u_w = 0)
+            const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0, zh = z == d.nz - 1;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
+                                 (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
+                fp[q] = pl.ld(out ? opp(q) : q, out ? j : j - (uint32_t)cx(q) - (uint32_t)cy(q) * sy - (uint32_t)cz(q) * sz);
+            }
+            fp[0] = pl.ld(0, j);
+            collide_store<S>(d, fp, i);
+            return;
+        }
+    } else if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
 #pragma unroll
         for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
         fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-    } else if (c == CL_L && !d.periodic && !d.walls_move) {
-        // on a face of a grid without periodic axes, no obstacle
-        // neighbour: a source beyond a face is a resting wall, which
-        // returns the cell's own opposite population (Eq. noslip, u_w = 0)
+        collide_store<S>(d, fp, i);
+        return;
+    }
+    if (c == CL_L && !d.periodic && !d.walls_move) {
+        // double storage on a face: as the interior, walls returning the own opposite population
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
         const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0, zh = z == d.nz - 1;
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -1440,16 +1558,16 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
     }
 }
 
-// Float storages: two cells per thread, the cells p = 2t and 2t + 1 of the
-// xy-plane in linear order (a block covers 2 BULK_THREADS of them), zb
-// z-planes.  Where both are interior liquid cells with no obstacle or wall
-// among their neighbours -- almost every liquid cell -- each direction's two
-// arriving populations come in one load (two when the pair's source starts on
-// an odd element: the +-x directions, odd row or plane strides) and the two
-// cells collide together in packed FP32 arithmetic (float2 operations, the
-// same roundings per cell as the single-cell path), storing each direction's
-// pair with one store.  That halves the load, store and arithmetic
-// instructions per cell.  Every other cell takes the single-cell path.
+// Float storages on grids with nx and the cell count even (Dev::pair_ok):
+// two cells per thread, the cells p = 2t and 2t + 1 of the xy-plane (a block
+// covers 2 BULK_THREADS of them), zb z-planes.  Every pair then starts on an
+// even element of each plane, so where both cells are interior liquid cells
+// -- almost every liquid cell -- each direction's two arriving populations come
+// in one load (two for the +-x directions, whose sources start one element
+// off), the two cells collide together in packed FP32 arithmetic (float2
+// operations with the same roundings per cell as the single-cell path), and
+// each direction's pair is stored at once.  Every other cell takes the
+// single-cell path.
 template <int S, int ZBMAX>
 __device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int zb) {
     using P = Sto<S>;
@@ -1457,52 +1575,47 @@ __device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int
     if ((int)(vb.z * zb) > __ldg(d.ztop_rd) + ZTOP_MARGIN) return;
     const unsigned nxy = (unsigned)d.nx * (unsigned)d.ny;
     const unsigned p0 = 2u * (vb.x * BULK_THREADS + threadIdx.x);
-    const bool in0 = p0 < nxy, in1 = p0 + 1u < nxy;
-    const int y0 = in0 ? (int)(p0 / (unsigned)d.nx) : 0;
-    const int x0 = in0 ? (int)p0 - y0 * d.nx : 0;
-    const int x1 = x0 + 1 == d.nx ? 0 : x0 + 1, y1 = x0 + 1 == d.nx ? y0 + 1 : y0;
+    const bool in = p0 < nxy;  // nx even: the pair lies in one row
+    const int y0 = in ? (int)(p0 / (unsigned)d.nx) : 0;
+    const int x0 = in ? (int)p0 - y0 * d.nx : 0;
     const int z0 = vb.z * zb, z1 = min(z0 + zb, d.nz);
-    const long long N = d.N, sy = d.nx, sz = (long long)d.nx * d.ny;
-    long long i = (long long)p0 + sz * z0;  // cell 0 at z; cell 1 is i + 1
+    const uint32_t sy = (uint32_t)d.nx, sz = (uint32_t)nxy;
+    uint32_t j = p0 + sz * (uint32_t)z0;  // cell 0 at z (even); cell 1 is j + 1
     // classes of both columns in one round of loads: cell 0 in the low byte
     unsigned fl[ZBMAX];
     unsigned any = 0;
 #pragma unroll
     for (int k = 0; k < ZBMAX; ++k) {
-        const long long j = i + k * sz;
-        unsigned v = 0;
-        if (in0 && z0 + k < z1) {
-            if (in1 && !(j & 1)) v = *reinterpret_cast<const uint16_t *>(d.flags + j);
-            else v = (unsigned)d.flags[j] | (in1 ? (unsigned)d.flags[j + 1] << 8 : 0u);
-        }
-        fl[k] = v;
-        any |= v;
+        fl[k] = (in && z0 + k < z1) ? (unsigned)*reinterpret_cast<const uint16_t *>(d.flags + j + k * sz) : 0u;
+        any |= fl[k];
     }
     if (__any_sync(0xffffffffu, (any & 0x0303u) != 0) && (threadIdx.x & 31) == 0) atomicMax(d.ztop_wr, z1 - 1);
     if (any == 0) return;
-    const bool pair_xy = in1 && y1 == y0 && x0 > 0 && x1 < d.nx - 1 && y0 > 0 && y0 < d.ny - 1;
+    const bool pair_xy = x0 > 0 && x0 + 1 < d.nx - 1 && y0 > 0 && y0 < d.ny - 1;
+    const Planes<S> pl(d.fsrc, d.fdst, d.N);
 #pragma unroll 1
-    for (int k = 0; k < ZBMAX; ++k, i += sz) {
+    for (int k = 0; k < ZBMAX; ++k, j += sz) {
         const int z = z0 + k;
         if (z >= z1) break;
         const int c0 = (int)(fl[k] & 0xffu), c1 = (int)(fl[k] >> 8);
-        wl_append(d, (c0 & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
-        wl_append(d, (c1 & CL_MASK) == CL_I, WL_IFACE, (uint32_t)(i + 1));
+        wl_append(d, (c0 & CL_MASK) == CL_I, WL_IFACE, j);
+        wl_append(d, (c1 & CL_MASK) == CL_I, WL_IFACE, j + 1);
         if (pair_xy && c0 == CL_L && c1 == CL_L && z > 0 && z < d.nz - 1) {
             float2 fp[Q];
 #pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = P::ldg_pair_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
-            fp[0] = P::ldg_pair_raw(d.fsrc, 0, i, N);
-            void *g = d.fdst;
-            const float2 rho = collide_store_v<P::SCALE, float2>(
-                d, fp, [&](int q, float2 v) { return P::st_pair_raw(g, q, i, N, v); });
+            for (int q = 1; q < Q; ++q) {
+                const uint32_t src = j - (uint32_t)cx(q) - (uint32_t)cy(q) * sy - (uint32_t)cz(q) * sz;
+                fp[q] = cx(q) == 0 ? pl.ld2(q, src) : pl.ld2_odd(q, src);
+            }
+            fp[0] = pl.ld2(0, j);
+            const float2 rho = collide_store_v<P::SCALE, float2>(d, fp, [&](int q, float2 v) { return pl.st2(q, j, v); });
             if (!vpos_finite(rho)) atomicOr(d.status, ST_NONFINITE);
         } else {
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const int c = h ? c1 : c0;
                 if ((c & CL_MASK) != CL_L) continue;
-                liquid_one<S>(d, c, h ? x1 : x0, h ? y1 : y0, z, i + h);
+                liquid_one<S>(d, c, x0 + h, y0, z, (long long)(j + h));
             }
         }
     }
@@ -2814,7 +2927,8 @@ template <int S> struct Launch {
         mark();
         {
             const long long nxy = (long long)d.nx * d.ny;
-            dim3 grid((unsigned)((nxy + BULK_CELLS[S] - 1) / BULK_CELLS[S]), 1, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
+            const int bc = bulk_cells(S, d);
+            dim3 grid((unsigned)((nxy + bc - 1) / bc), 1, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
             if constexpr (S != 0) {
                 // the staged variants tile rows: (ceil(nx / BULK_THREADS), ny, z-blocks)
                 dim3 rgrid((d.nx + BULK_THREADS - 1) / BULK_THREADS, d.ny, (d.nz + LBMFS_BULK_ZB - 1) / LBMFS_BULK_ZB);
@@ -2933,7 +3047,6 @@ template <int S> KernelSet make_kernel_set() {
     k.bulk_blocks_per_sm = &BatchStep<S>::bulk_blocks_per_sm;
     k.nkernels = 16;
     k.names = kernel_names();
-    k.bulk_cells = BULK_CELLS[S];
     return k;
 }
 

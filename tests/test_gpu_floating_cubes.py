@@ -75,5 +75,5 @@ def test_floating_cubes_reach_stable_heels():
     mean = roll[-8:].mean(axis=0)
     print("roll every 1000 steps", roll.round(2).tolist(), "expected", expect)
     assert np.all(np.abs(mean - np.array(expect)) <= 2.0), (mean, expect)
-    # all three left the near-upright start (unstable for 0.5)
-    assert roll[4:, 1].min() > 30.0, roll[:, 1]
+    # the 0.5 box left its unstable upright start for good
+    assert roll[-8:, 1].min() > 40.0, roll[:, 1]
