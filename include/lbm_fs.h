@@ -124,7 +124,7 @@ typedef struct {
     /* Readings of the paper where it is silent.  A field below is used only
      * when its LBM_FS_READING_* bit is set in `readings`; otherwise its default
      * applies (a zeroed struct gets every default).
-     *  normal_deadband (default 1e-3, >= 0): Eq. reconstruct rebuilds the
+     *  normal_deadband (default 1e-2, >= 0): Eq. reconstruct rebuilds the
      *    populations of the directions with c_q . n <= 0 (Sec. 2.2); a
      *    direction counts when c_q . n < -normal_deadband.  0 is the bare
      *    sign test, under which the noise of the estimated normal decides the

@@ -22,7 +22,7 @@
  * Eq. forceterm are garbled), the cell's own density in the moving-wall term,
  * u_w at the link midpoint, the anti-bounce-back of the cell's own outgoing
  * population in Eq. reconstruct, a central-difference normal with
- * c.n < -deadband (default 1e-3, a dead band against noise; 0 gives the bare
+ * c.n < -deadband (default 1e-2, a dead band against noise; 0 gives the bare
  * sign test), eps = 1e-2, Jacobi-style conversions with equal excess-mass
  * split, and the obstacle-to-fluid priority interface > liquid > gas.  The
  * readings that are options (dead band, the neighbour conversion rule, the
@@ -47,10 +47,10 @@ enum { M_FIXED = 0, M_FREE = 1, M_ROT_AXIS = 2, M_DAMP = 0x100 };
  * tangential to a flat surface has c_q . n = 0 up to noise (rounding, storage
  * precision), and a bare sign test turns that noise into a discontinuous
  * reconstruct / stream decision; by default directions count as pointing out
- * of the gas only when c_q . n < -1e-3, i.e. when the fill level changes by
- * more than 2e-3 across the cell (orc_set_readings changes it; 0 is the
+ * of the gas only when c_q . n < -1e-2, i.e. when the fill level changes by
+ * more than 2e-2 across the cell (orc_set_readings changes it; 0 is the
  * strict sign test c_q . n < 0). */
-#define DEFAULT_DEADBAND 1e-3
+#define DEFAULT_DEADBAND 1e-2
 
 /* D3Q19 velocities in the order of the paper's stencil figure. */
 static const int C[Q][3] = {

@@ -75,7 +75,7 @@ void orc_set_surface_tension(orc_sim *s, double sigma);
 /* velocities of the wall faces x-, x+, y-, y+, z-, z+ (3 each; Eq. noslip
  * with u_w at domain walls); zero by default */
 void orc_set_wall_velocity(orc_sim *s, const double v[18]);
-/* readings where the paper is silent (defaults 1e-3, 1, 1, 1):
+/* readings where the paper is silent (defaults 1e-2, 1, 1, 1):
  *   deadband       Eq. reconstruct rebuilds a direction when c_q . n < -deadband
  *                  (0: the strict sign test);
  *   virtual_mass   C of the rigid-body update (0: explicit Newton update);

@@ -145,7 +145,7 @@ class OracleSim:
             self.lib.orc_destroy(self.h)
             self.h = None
 
-    def set_readings(self, deadband: float = 1e-3, virtual_mass: float = 1.0, force_mean: bool = True,
+    def set_readings(self, deadband: float = 1e-2, virtual_mass: float = 1.0, force_mean: bool = True,
                      neighbour_rule: bool = True):
         """The options where the paper is silent (C declaration of orc_set_readings)."""
         self.lib.orc_set_readings(self.h, float(deadband), float(virtual_mass), int(bool(force_mean)),

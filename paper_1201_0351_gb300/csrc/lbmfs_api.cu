@@ -192,7 +192,7 @@ lbm_fs_status lbm_fs_create(const lbm_fs_params *p, lbm_fs **out) {
     d.sigma = p->sigma;
     d.sigma_f = (float)p->sigma;
     d.cap = (uint32_t)N;
-    d.deadband = rd_db ? p->normal_deadband : 1e-3;
+    d.deadband = rd_db ? p->normal_deadband : 1e-2;
     d.deadband_f = (float)d.deadband;
     d.vmass = rd_vm ? p->virtual_mass : 1.0;
     d.force_mean = (p->readings & LBM_FS_READING_FORCE_MEAN) ? (p->force_mean != 0) : 1;

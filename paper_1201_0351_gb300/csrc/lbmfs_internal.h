@@ -23,7 +23,7 @@ constexpr int BULK_THREADS = LBMFS_BULK_THREADS;  // x extent of a bulk-kernel b
 // cells of an xy-plane per bulk-kernel block, by storage: one per thread for
 // double, two per thread for the float storages
 #ifndef LBMFS_BULK_PAIR
-#define LBMFS_BULK_PAIR 1  // float storages on even grids: two cells per bulk-kernel thread
+#define LBMFS_BULK_PAIR 0  // tuning knob: float storages on even grids take two cells per bulk-kernel thread
 #endif
 
 // cell classes (as in the C ABI) in the low nibble of the flag byte; bit 4

@@ -63,7 +63,7 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 #define LBMFS_BULK_MINB 8  // resident blocks per SM asked of ptxas for the bulk kernel (64 registers)
 #endif
 #ifndef LBMFS_BULK_PAIR
-#define LBMFS_BULK_PAIR 1  // float storages: two cells per bulk-kernel thread
+#define LBMFS_BULK_PAIR 0  // tuning knob: float storages on even grids take two cells per bulk-kernel thread
 #endif
 #ifndef LBMFS_PAIR_MINB
 #define LBMFS_PAIR_MINB 5  // resident blocks per SM of the two-cell bulk kernel (float storages, 96 registers)
@@ -1413,9 +1413,9 @@ __device__ __forceinline__ void collide_store(const Dev &d, typename Sto<S>::R *
         if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
     } else {
         // fp in the storage's raw units (to_raw)
-        const Planes<S> pl(d.fsrc, d.fdst, d.N);
-        const uint32_t j = (uint32_t)i;
-        float rho = collide_store_v<P::SCALE, float>(d, fp, [&](int q, float v) { return pl.st(q, j, v); });
+        void *g = d.fdst;
+        const long long N = d.N;
+        float rho = collide_store_v<P::SCALE, float>(d, fp, [&](int q, float v) { return P::st_raw(g, q, i, N, v); });
         if (!vpos_finite(rho)) atomicOr(d.status, ST_NONFINITE);
     }
 }
@@ -1470,34 +1470,9 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
     using R = typename P::R;
     const long long N = d.N;
     R fp[Q];
-    if constexpr (S != 0) {
-        const Planes<S> pl(d.fsrc, d.fdst, N);
-        const uint32_t j = (uint32_t)i, sy = (uint32_t)d.nx, sz = (uint32_t)d.nx * (uint32_t)d.ny;
-        if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-            // no obstacle or wall in the neighbourhood and a liquid cell never
-            // touches gas: plain pull from the 18 neighbours
-#pragma unroll
-            for (int q = 1; q < Q; ++q) fp[q] = pl.ld(q, j - (uint32_t)cx(q) - (uint32_t)cy(q) * sy - (uint32_t)cz(q) * sz);
-            fp[0] = pl.ld(0, j);
-            collide_store<S>(d, fp, i);
-            return;
-        }
-        if (c == CL_L && !d.periodic && !d.walls_move) {
-            // on a face of a grid without periodic axes, no obstacle
-            // neighbour: a source beyond a face is a resting wall, which
-            // returns the cell's own opposite population (Eq. noslip, u_w = 0)
-            const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0, zh = z == d.nz - 1;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const bool out = (cx(q) > 0 && xl) || (cx(q) < 0 && xh) || (cy(q) > 0 && yl) || (cy(q) < 0 && yh) ||
-                                 (cz(q) > 0 && zl) || (cz(q) < 0 && zh);
-                fp[q] = pl.ld(out ? opp(q) : q, out ? j : j - (uint32_t)cx(q) - (uint32_t)cy(q) * sy - (uint32_t)cz(q) * sz);
-            }
-            fp[0] = pl.ld(0, j);
-            collide_store<S>(d, fp, i);
-            return;
-        }
-    } else if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+    if (c == CL_L && x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+        // no obstacle or wall in the neighbourhood and a liquid cell never
+        // touches gas: plain pull from the 18 neighbours
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
 #pragma unroll
         for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
@@ -1506,7 +1481,9 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
         return;
     }
     if (c == CL_L && !d.periodic && !d.walls_move) {
-        // double storage on a face: as the interior, walls returning the own opposite population
+        // on a face of a grid without periodic axes, no obstacle
+        // neighbour: a source beyond a face is a resting wall, which
+        // returns the cell's own opposite population (Eq. noslip, u_w = 0)
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
         const bool xl = x == 0, xh = x == d.nx - 1, yl = y == 0, yh = y == d.ny - 1, zl = z == 0, zh = z == d.nz - 1;
 #pragma unroll
@@ -2072,6 +2049,31 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             float fo[Q], fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
+            // the sources' classes, then their populations and fill levels (below);
+            // a source index is recomputed rather than held (registers)
+            const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+            const uint32_t syu = (uint32_t)d.nx, szu = (uint32_t)d.nx * (uint32_t)d.ny;
+            auto src = [&](int q) -> long long {
+                if (inner) return (long long)((uint32_t)i - (uint32_t)cx(q) - (uint32_t)cy(q) * syu - (uint32_t)cz(q) * szu);
+                return nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            };
+            // class codes, 3 bits per direction: 1 liquid, 2 interface, 3 gas, 4 obstacle, 5 wall
+            uint64_t ncode = 0;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const long long si = src(q);
+                const int c = si < 0 ? CL_WALL : (int)(d.flags[si] & CL_MASK);
+                const uint64_t code = c == CL_L ? 1u : (c == CL_I ? 2u : (c == CL_G ? 3u : (c == CL_O ? 4u : 5u)));
+                ncode |= code << (3 * q);
+            }
+            float pull[Q], phs[Q];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const unsigned code = (unsigned)(ncode >> (3 * q)) & 7u;
+                const long long si = src(q);
+                pull[q] = (code == 1u || code == 2u) ? P::ld(d.fsrc, q, si, N) : 0.0f;
+                phs[q] = code == 2u ? (float)d.phisrc[si] : 0.0f;
+            }
             float drx = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -2082,13 +2084,18 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             }
             float rx = 1.0f + drx;
             float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
-            // One walk over the 18 neighbours s = x - c_q: the class decides the
+            // The 18 neighbours s = x - c_q in two rounds of independent
+            // requests (a walk that waits on each class before the next
+            // request costs one memory latency per direction): first every
+            // source's class, then every pulled population and every
+            // interface neighbour's fill level.  The class decides the
             // arriving population (pull, or Eq. noslip from an obstacle or a
-            // wall; gas sources are reconstructed below); a liquid or interface
-            // source also gives the Sec. 2.2 mass exchange of the link back to
-            // it, f_q(s) - f_qbar(x) (weighted by the mean fill for interface
-            // neighbours), and the axis neighbours give the fill levels of the
-            // normal (1 / phi / 0 for liquid / interface / gas, own phi else).
+            // wall; gas sources are reconstructed below); a liquid or
+            // interface source also gives the Sec. 2.2 mass exchange of the
+            // link back to it, f_q(s) - f_qbar(x) (weighted by the mean fill
+            // for interface neighbours), and the axis neighbours give the fill
+            // levels of the normal (1 / phi / 0 for liquid / interface / gas,
+            // own phi else).
             fp[0] = fo[0];
             unsigned solid = 0, gas = 0;  // directions whose source is solid / gas
             bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
@@ -2097,14 +2104,14 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const int qb = opp(q);
-                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                const int ns = cls(d, si);
+                const unsigned code = (unsigned)(ncode >> (3 * q)) & 7u;
+                const int ns = code == 1u ? CL_L : (code == 2u ? CL_I : (code == 3u ? CL_G : (code == 4u ? CL_O : CL_WALL)));
                 has_l = has_l || ns == CL_L;
                 has_g = has_g || ns == CL_G;
                 float seen = phx;
                 if (ns == CL_WALL || ns == CL_O) {
                     solid |= 1u << q;
-                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
+                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[src(q)]], x, y, z, q)
                                            : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
                     fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
                 } else if (ns == CL_G) {
@@ -2112,13 +2119,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                     fp[q] = 0.0f;
                     seen = 0.0f;
                 } else {
-                    const float pq = P::ld(d.fsrc, q, si, N);
+                    const float pq = pull[q];
                     fp[q] = pq;
                     if (ns == CL_L) {
                         dm += pq - fo[qb];
                         seen = 1.0f;
                     } else {
-                        const float phy = (float)d.phisrc[si];
+                        const float phy = phs[q];
                         dm += 0.5f * (phx + phy) * (pq - fo[qb]);
                         seen = phy;
                     }

@@ -100,7 +100,7 @@ class Scenario:
     sigma: float = 0.0  # surface tension (Laplace pressure 2 sigma kappa at the interface); 0 = none
     wall_vel: Optional[tuple] = None  # 18 floats: velocity of the faces x-, x+, y-, y+, z-, z+; None = at rest
     # options where the paper is silent, as keyword values (deadband, virtual_mass,
-    # force_mean, neighbour_rule); None = each side's defaults (1e-3, 1, True, True)
+    # force_mean, neighbour_rule); None = each side's defaults (1e-2, 1, True, True)
     readings: Optional[dict] = None
 
     @property

@@ -120,7 +120,7 @@ def test_strict_sign_test_breaks_the_planar_bound():
     (dead band 0) the noise of the estimated normal decides the tangential
     directions of a flat surface cell by cell, and the spurious interface
     velocities of the same closed tank exceed the paper's 1e-5 several times
-    over (measured 7e-5); with the 1e-3 dead band they stay below it (previous
+    over (measured 7e-5); with the default dead band they stay below it (previous
     test).  The surface stays one layer thick either way."""
     zs, spread, dev, err = _planar(I.closed_tank_32(with_box=False), 200, deadband=0.0)
     assert list(zs) == [16] and err == 0
