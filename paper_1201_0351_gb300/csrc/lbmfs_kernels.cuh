@@ -1477,10 +1477,7 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
 #pragma unroll
         for (int q = 1; q < Q; ++q) fp[q] = P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
         fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-        collide_store<S>(d, fp, i);
-        return;
-    }
-    if (c == CL_L && !d.periodic && !d.walls_move) {
+    } else if (c == CL_L && !d.periodic && !d.walls_move) {
         // on a face of a grid without periodic axes, no obstacle
         // neighbour: a source beyond a face is a resting wall, which
         // returns the cell's own opposite population (Eq. noslip, u_w = 0)
@@ -1506,7 +1503,7 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
         gather_general<S>(d, x, y, z, i, fp);
         to_raw<S>(fp);
     }
-    collide_store<S>(d, fp, i);
+    collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
 }
 
 // The cells (x, y, z0 .. z1-1) of one thread.  The flags of the whole column
