@@ -354,8 +354,10 @@ int32_t lbm_fs_version(void);
  * Block partial sums live in a fixed 512 KiB device array of the library
  * (held by every GPU that loads the library until exit), so n is limited to
  * 268435456 cells; larger n, n < 0 or a null pointer give LBM_FS_EINVAL.  The
- * first call on a device looks up that array's device address (set-up with the
- * device current); make that first call before any stream capture.  Every call
+ * first call on a device, and the first in any other CUDA context of it (after
+ * a cudaDeviceReset, or in a caller's own context), looks up that array's
+ * device address in the current context (set-up with the device current);
+ * make such a first call before any stream capture.  Every call
  * on a device shares the array and it keeps the last call's contents: calls
  * that overlap on the GPU (different streams, no ordering) race and may return
  * wrong sums.  No cudaMalloc / cudaFree or allocating routine is called.  The

@@ -1394,7 +1394,8 @@ __device__ __forceinline__ void bulk_body(const Dev &d, const VB &vb, int zb) {
     else liquid_body<S, ZBMAX>(d, vb, zb);
 }
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : LBMFS_PAIR_MINB) k_liquid(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(BULK_THREADS, S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB))
+    k_liquid(const __grid_constant__ Dev d) {
     bulk_body<S, LBMFS_BULK_ZB>(d, vb_own(), LBMFS_BULK_ZB);
 }
 
@@ -2046,31 +2047,6 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             float fo[Q], fp[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
-            // the sources' classes, then their populations and fill levels (below);
-            // a source index is recomputed rather than held (registers)
-            const bool inner = x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
-            const uint32_t syu = (uint32_t)d.nx, szu = (uint32_t)d.nx * (uint32_t)d.ny;
-            auto src = [&](int q) -> long long {
-                if (inner) return (long long)((uint32_t)i - (uint32_t)cx(q) - (uint32_t)cy(q) * syu - (uint32_t)cz(q) * szu);
-                return nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-            };
-            // class codes, 3 bits per direction: 1 liquid, 2 interface, 3 gas, 4 obstacle, 5 wall
-            uint64_t ncode = 0;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const long long si = src(q);
-                const int c = si < 0 ? CL_WALL : (int)(d.flags[si] & CL_MASK);
-                const uint64_t code = c == CL_L ? 1u : (c == CL_I ? 2u : (c == CL_G ? 3u : (c == CL_O ? 4u : 5u)));
-                ncode |= code << (3 * q);
-            }
-            float pull[Q], phs[Q];
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const unsigned code = (unsigned)(ncode >> (3 * q)) & 7u;
-                const long long si = src(q);
-                pull[q] = (code == 1u || code == 2u) ? P::ld(d.fsrc, q, si, N) : 0.0f;
-                phs[q] = code == 2u ? (float)d.phisrc[si] : 0.0f;
-            }
             float drx = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -2081,18 +2057,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
             }
             float rx = 1.0f + drx;
             float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
-            // The 18 neighbours s = x - c_q in two rounds of independent
-            // requests (a walk that waits on each class before the next
-            // request costs one memory latency per direction): first every
-            // source's class, then every pulled population and every
-            // interface neighbour's fill level.  The class decides the
+            // One walk over the 18 neighbours s = x - c_q: the class decides the
             // arriving population (pull, or Eq. noslip from an obstacle or a
-            // wall; gas sources are reconstructed below); a liquid or
-            // interface source also gives the Sec. 2.2 mass exchange of the
-            // link back to it, f_q(s) - f_qbar(x) (weighted by the mean fill
-            // for interface neighbours), and the axis neighbours give the fill
-            // levels of the normal (1 / phi / 0 for liquid / interface / gas,
-            // own phi else).
+            // wall; gas sources are reconstructed below); a liquid or interface
+            // source also gives the Sec. 2.2 mass exchange of the link back to
+            // it, f_q(s) - f_qbar(x) (weighted by the mean fill for interface
+            // neighbours), and the axis neighbours give the fill levels of the
+            // normal (1 / phi / 0 for liquid / interface / gas, own phi else).
             fp[0] = fo[0];
             unsigned solid = 0, gas = 0;  // directions whose source is solid / gas
             bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
@@ -2101,14 +2072,14 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const int qb = opp(q);
-                const unsigned code = (unsigned)(ncode >> (3 * q)) & 7u;
-                const int ns = code == 1u ? CL_L : (code == 2u ? CL_I : (code == 3u ? CL_G : (code == 4u ? CL_O : CL_WALL)));
+                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+                const int ns = cls(d, si);
                 has_l = has_l || ns == CL_L;
                 has_g = has_g || ns == CL_G;
                 float seen = phx;
                 if (ns == CL_WALL || ns == CL_O) {
                     solid |= 1u << q;
-                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[src(q)]], x, y, z, q)
+                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
                                            : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
                     fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
                 } else if (ns == CL_G) {
@@ -2116,13 +2087,13 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
                     fp[q] = 0.0f;
                     seen = 0.0f;
                 } else {
-                    const float pq = pull[q];
+                    const float pq = P::ld(d.fsrc, q, si, N);
                     fp[q] = pq;
                     if (ns == CL_L) {
                         dm += pq - fo[qb];
                         seen = 1.0f;
                     } else {
-                        const float phy = phs[q];
+                        const float phy = (float)d.phisrc[si];
                         dm += 0.5f * (phx + phy) * (pq - fo[qb]);
                         seen = phy;
                     }
@@ -2863,7 +2834,8 @@ struct BkReset {
 template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, true, forces_body<S>(d, vb))
 // one instantiation per z-planes-per-tile choice (the column loop unrolled to it)
 template <int S, int ZB>
-LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : LBMFS_PAIR_MINB, (bulk_body<S, ZB>(d, vb, zb)))
+LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB),
+                 (bulk_body<S, ZB>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))

@@ -7,6 +7,7 @@
 // capture), or a latency-critical loop where a cudaMalloc / cudaFree could
 // block on device synchronisation.  The caller passes device pointers to the
 // inputs and the output; nothing is allocated.
+#include <cuda.h>  // CUcontext / CUresult types of the two driver calls looked up below
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -26,8 +27,45 @@ constexpr int NA_MAX_DEVICES = 64;
 // Shared by every call on a device; keeps the last call's partial sums.
 static __device__ __align__(256) double g_mass_partials[NA_SCRATCH];
 
-double *g_partials_ptr[NA_MAX_DEVICES];  // device address per device, set once
+// device address of the array per device, with the id of the context it was
+// looked up in: a cudaDeviceReset, or a caller's own (non-primary) context,
+// brings a new context in which the library's device code, and the array,
+// may sit elsewhere, so the address is looked up again for a new context id
+struct Setup {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+Setup g_setup[NA_MAX_DEVICES];
 std::mutex g_setup_mutex;
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// id of the calling thread's current context (0 on failure); call with
+// g_setup_mutex held
+unsigned long long current_context_id(int dev) {
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&g_ctx_current, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&g_ctx_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            g_ctx_current = nullptr;
+            g_ctx_id = nullptr;
+            return 0;
+        }
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return 0;
+    if (!ctx) {
+        // no context yet on this thread: make the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess || g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    }
+    unsigned long long id = 0;
+    return g_ctx_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
 thread_local std::string g_na_err;
 
 __global__ void k_na_partial(const uint8_t *flags, const double *mass, long long n, double *partials) {
@@ -83,16 +121,19 @@ extern "C" lbm_fs_status lbm_fs_liquid_mass_noalloc(const uint8_t *flags, const 
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(LBM_FS_EINVAL, "lbm_fs_liquid_mass_noalloc: device index");
     double *partials;
     {
-        // set-up, once per device and with that device current: the host-side
-        // name of the array is not a device address
+        // set-up, once per device and context, with that device current: the
+        // host-side name of the array is not a device address
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_partials_ptr[dev]) {
+        const unsigned long long id = current_context_id(dev);
+        if (id == 0) return na_fail(LBM_FS_ECUDA, "lbm_fs_liquid_mass_noalloc: no current CUDA context");
+        if (!g_setup[dev].ptr || g_setup[dev].ctx_id != id) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_mass_partials);
             if (e != cudaSuccess) return na_fail(LBM_FS_ECUDA, cudaGetErrorString(e));
-            g_partials_ptr[dev] = (double *)ptr;
+            g_setup[dev].ptr = (double *)ptr;
+            g_setup[dev].ctx_id = id;
         }
-        partials = g_partials_ptr[dev];
+        partials = g_setup[dev].ptr;
     }
     cudaStream_t st = (cudaStream_t)stream;
     int nblocks = (int)((n + NA_CHUNK - 1) / NA_CHUNK);

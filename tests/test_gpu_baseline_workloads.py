@@ -11,7 +11,7 @@
 * Stratified channel (Sec. 3.2.1, free advection): 96 x 32 x 32, periodic in x,
   body force 1e-6 along x, a free 8 x 8 x 6 box of density 0.5, 5000 steps in
   FP64 and FP32: the box drifts with the surface layer; the FP32 run agrees
-  with the FP64 run cell by cell for the first 500 steps and in the box's
+  with the FP64 run cell by cell for the first 1000 steps and in the box's
   drift and the surface velocity over all 5000 (the error growth is printed).
 """
 import dataclasses
@@ -83,9 +83,8 @@ def test_heeled_box_righting_moment(heeled_fixed, storage):
 
 def test_heeled_box_reduced_precision_torque():
     """the torque of the FP32 and FP16 runs against the FP64 path (itself equal
-    to the oracle bit for bit) over the first 200 steps, within the storages'
-    tolerances of |T|; the difference after 2000 steps, which grows over the
-    run, is printed"""
+    to the oracle bit for bit): FP32 within 1e-5 of |T| over 2000 steps, FP16
+    within 2e-3 over the first 200 (its difference at 2000 steps is printed)"""
     from paper_1201_0351_gb300 import lbm_fs
 
     sims = {s: lbm_fs.Simulation(I.heeled_box_128(fixed=True), storage=s) for s in ("f64", "f32", "f16s")}
@@ -97,8 +96,9 @@ def test_heeled_box_reduced_precision_torque():
         t = {k: sim.body(0)["T"][0] for k, sim in sims.items()}
         rel = {k: abs(t[k] - t["f64"]) / abs(t["f64"]) for k in ("f32", "f16s")}
         print("step", target, "T_x FP64", t["f64"], "relative difference", rel)
+        worst["f32"] = max(worst["f32"], rel["f32"])
         if target <= 200:
-            worst = {k: max(worst[k], rel[k]) for k in rel}
+            worst["f16s"] = max(worst["f16s"], rel["f16s"])
     for sim in sims.values():
         sim.close()
     assert worst["f32"] <= 1e-5 and worst["f16s"] <= 2e-3, worst
@@ -139,7 +139,7 @@ def channel_5000():
             strip = (fl == I.INTERFACE) & (np.abs(y - b["center"][1]) <= 4.0)
             rec[s]["vx"].append(b["vel"][0])
             rec[s]["strip"].append(f["u"].reshape(32, 32, 96, 3)[strip][:, 0].mean())
-            if (k + 1) * 100 in (500, 5000):
+            if (k + 1) * 100 in (1000, 5000):
                 rec[s]["fields"][(k + 1) * 100] = f
             rec[s]["stats"] = sim.stats()
     for sim in sims.values():
@@ -163,17 +163,15 @@ def test_channel_box_drifts_with_the_surface(channel_5000):
 
 def test_channel_f32_against_f64_over_5000_steps(channel_5000):
     """FP32 storage against the FP64 path (itself equal to the oracle bit for
-    bit), 5000 steps.  Cell by cell the fields agree within 1e-5 while the
-    moving box's cover / uncover events fall on the same steps (checked at 500
-    steps); later an event one step apart leaves a local difference near the
-    box that the flow keeps (printed), while the box's drift and the mean
-    surface velocity -- the quantities the test measures -- agree to 1e-2."""
+    bit), 5000 steps: cell by cell within 1e-5 after 1000 steps; the box's
+    drift and the surface velocity of its strip within 1e-4 over the whole
+    run (the cell-by-cell error after 5000 steps is printed)"""
     f64, f32 = channel_5000["f64"], channel_5000["f32"]
-    e500 = macro_errors(f32["fields"][500], f64["fields"][500])
+    e1000 = macro_errors(f32["fields"][1000], f64["fields"][1000])
     e5000 = macro_errors(f32["fields"][5000], f64["fields"][5000])
     dv = np.abs(np.array(f32["vx"]) - np.array(f64["vx"])) / np.abs(f64["vx"]).max()
     ds = np.abs(np.array(f32["strip"]) - np.array(f64["strip"])) / np.abs(f64["strip"]).max()
-    print("500 steps", e500, "5000 steps", e5000, "box vx difference every 1000 steps", dv[9::10],
+    print("1000 steps", e1000, "5000 steps", e5000, "box vx difference every 1000 steps", dv[9::10],
           "strip surface difference", ds[9::10])
-    assert e500["flag_diff"] == 0 and e500["rho"] <= 1e-5 and e500["u"] <= 1e-5, e500
-    assert dv.max() <= 1e-2 and ds.max() <= 1e-2, (dv.max(), ds.max())
+    assert e1000["flag_diff"] == 0 and e1000["rho"] <= 1e-5 and e1000["u"] <= 1e-5, e1000
+    assert dv.max() <= 1e-4 and ds.max() <= 1e-4, (dv.max(), ds.max())
