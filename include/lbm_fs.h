@@ -311,12 +311,16 @@ lbm_fs_status lbm_fs_batch_sync(lbm_fs_batch *b);
  *   bulk_blocks persistent grid of the bulk kernel (0: one block per tile);
  *   list_cells  nx*ny cells of a tank per block of the worklist kernels
  *               (a tank gets ceil(nx*ny / list_cells) blocks, at most 304);
+ *   lanes       groups of tanks (of about equal cell count) whose step
+ *               launches form independent chains that the GPU runs side by
+ *               side, one group's short list kernels beside another's bulk
+ *               kernel (1..4; 0 keeps the current value; default 2);
  *   bulk_ms     (autotune output) time of one bulk launch with this setting. */
 typedef struct {
     int32_t zb;
     int32_t bulk_blocks;
     int32_t list_cells;
-    int32_t pad;
+    int32_t lanes;
     double bulk_ms;
 } lbm_fs_batch_config_t;
 

@@ -23,10 +23,14 @@ namespace {
 
 constexpr int ZB_DEFAULT = 4;
 constexpr int LIST_CELLS_DEFAULT = 512;
+constexpr int LANES_DEFAULT = 2;
+
+constexpr int MAX_LANES = 4;
 
 // a group of at most BATCH_TANKS tanks served by the same launches
 struct Chunk {
-    int first = 0, count = 0;
+    std::vector<int> idx;  // the batch's tank indices, in descriptor order
+    int lane = 0;          // concurrent chain the chunk's launches belong to
     TankSet ts[2];         // descriptors for even / odd steps
     Shape sh[SH_COUNT];
 };
@@ -42,6 +46,9 @@ struct lbm_fs_batch {
     int zb = ZB_DEFAULT;
     int bulk_blocks = 0;  // 0: one block per bulk tile
     int list_cells = LIST_CELLS_DEFAULT;
+    int lanes = 1;  // groups of tanks whose step chains run concurrently
+    cudaStream_t lane_st[MAX_LANES] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[MAX_LANES] = {};
     std::vector<std::unique_ptr<Chunk>> chunks;
     std::vector<int> nb_built;  // bodies per tank when the tables were built
     bool built = false;
@@ -115,14 +122,14 @@ lbm_fs_status build(lbm_fs_batch *b) {
         Chunk &c = *cp;
         for (int k = 0; k < 2; ++k) {
             memset(&c.ts[k], 0, sizeof(TankSet));
-            for (int j = 0; j < c.count; ++j) c.ts[k].d[j] = b->tanks[c.first + j]->d[k];
+            for (int j = 0; j < (int)c.idx.size(); ++j) c.ts[k].d[j] = b->tanks[c.idx[j]]->d[k];
         }
         std::vector<Tile> tb[SH_COUNT];
-        for (int j = 0; j < c.count; ++j) {
-            const lbm_fs *t = b->tanks[c.first + j];
+        for (int j = 0; j < (int)c.idx.size(); ++j) {
+            const lbm_fs *t = b->tanks[c.idx[j]];
             const Dev &d = t->d[0];
             const int nb = t->nb;
-            b->nb_built[c.first + j] = nb;
+            b->nb_built[c.idx[j]] = nb;
             tb[SH_TANK].push_back(tile(j, 0, 0, 0, 1, 1, 1));
             for (int y = 0; y < nb; ++y)
                 for (int x = 0; x < FORCE_BLOCKS; ++x) tb[SH_FORCE].push_back(tile(j, x, y, 0, FORCE_BLOCKS, nb, 1));
@@ -180,9 +187,51 @@ BatchLaunch launch_of(lbm_fs_batch *b, Chunk &c, int parity) {
     return L;
 }
 
+// Split the tanks into b->lanes groups of about equal cell count (largest
+// first, each to the lightest group) and the groups into chunks of at most
+// BATCH_TANKS tanks.
+void make_chunks(lbm_fs_batch *b) {
+    const int nt = (int)b->tanks.size();
+    std::vector<int> order(nt);
+    for (int k = 0; k < nt; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->tanks[a]->d[0].N > b->tanks[c]->d[0].N; });
+    std::vector<std::vector<int>> lane(b->lanes);
+    std::vector<long long> load(b->lanes, 0);
+    for (int k : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[l].push_back(k);
+        load[l] += b->tanks[k]->d[0].N;
+    }
+    b->chunks.clear();
+    for (int l = 0; l < b->lanes; ++l) {
+        std::sort(lane[l].begin(), lane[l].end());
+        for (size_t first = 0; first < lane[l].size(); first += BATCH_TANKS) {
+            auto c = std::make_unique<Chunk>();
+            c->lane = l;
+            c->idx.assign(lane[l].begin() + first, lane[l].begin() + std::min(lane[l].size(), first + BATCH_TANKS));
+            b->chunks.push_back(std::move(c));
+        }
+    }
+    b->built = false;
+}
+
+// One step of every tank.  With several lanes the lanes' launch chains fork
+// from st and join back into it, so their kernels may run at the same time
+// (one lane's short list kernels beside another's bulk kernel).
 int enqueue_step(lbm_fs_batch *b, int parity, cudaStream_t st) {
     int n = 0;
-    for (auto &cp : b->chunks) n += b->ks.batch_step(launch_of(b, *cp, parity), st, nullptr);
+    if (b->lanes == 1) {
+        for (auto &cp : b->chunks) n += b->ks.batch_step(launch_of(b, *cp, parity), st, nullptr);
+        return n;
+    }
+    cudaEventRecord(b->fork_ev, st);
+    for (int l = 0; l < b->lanes; ++l) {
+        cudaStreamWaitEvent(b->lane_st[l], b->fork_ev, 0);
+        for (auto &cp : b->chunks)
+            if (cp->lane == l) n += b->ks.batch_step(launch_of(b, *cp, parity), b->lane_st[l], nullptr);
+        cudaEventRecord(b->join_ev[l], b->lane_st[l]);
+        cudaStreamWaitEvent(st, b->join_ev[l], 0);
+    }
     return n;
 }
 
@@ -232,6 +281,11 @@ void destroy_all(lbm_fs_batch *b) {
         lbm_fs_destroy(t);
     }
     if (b->cap_st) cudaStreamDestroy(b->cap_st);
+    for (int l = 0; l < MAX_LANES; ++l) {
+        if (b->lane_st[l]) cudaStreamDestroy(b->lane_st[l]);
+        if (b->join_ev[l]) cudaEventDestroy(b->join_ev[l]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
 }
 
@@ -256,8 +310,13 @@ lbm_fs_status lbm_fs_batch_create(const lbm_fs_params *params, int32_t count, lb
     b->dev_free = params[0].dev_free;
     b->alloc_ctx = params[0].alloc_ctx;
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking);
+    for (int l = 0; l < MAX_LANES && e == cudaSuccess; ++l) {
+        e = cudaStreamCreateWithFlags(&b->lane_st[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[l], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete b;
+        destroy_all(b);
         return cuda_fail(e, "cudaStreamCreate (batch)");
     }
     int dev = 0;
@@ -280,12 +339,8 @@ lbm_fs_status lbm_fs_batch_create(const lbm_fs_params *params, int32_t count, lb
         b->tanks.push_back(t);
     }
     b->ks = b->tanks[0]->ks;
-    for (int32_t first = 0; first < count; first += BATCH_TANKS) {
-        auto c = std::make_unique<Chunk>();
-        c->first = first;
-        c->count = std::min<int32_t>(BATCH_TANKS, count - first);
-        b->chunks.push_back(std::move(c));
-    }
+    b->lanes = std::max(1, std::min(LANES_DEFAULT, count));
+    make_chunks(b);
     *out = b;
     return LBM_FS_OK;
 }
@@ -353,20 +408,27 @@ lbm_fs_status lbm_fs_batch_get_config(lbm_fs_batch *b, lbm_fs_batch_config_t *c)
     c->zb = b->zb;
     c->bulk_blocks = b->bulk_blocks;
     c->list_cells = b->list_cells;
+    c->lanes = b->lanes;
     return LBM_FS_OK;
 }
 
 lbm_fs_status lbm_fs_batch_set_config(lbm_fs_batch *b, const lbm_fs_batch_config_t *c) {
     lbm_fs_status s = check_batch(b);
     if (s) return s;
-    if (!c || c->zb < 1 || c->zb > 8 || c->bulk_blocks < 0 || c->list_cells < 1)
-        return fail(LBM_FS_EINVAL, "config needs zb in 1..8, bulk_blocks >= 0, list_cells >= 1%s");
+    if (!c || c->zb < 1 || c->zb > 8 || c->bulk_blocks < 0 || c->list_cells < 1 || c->lanes < 0 ||
+        c->lanes > MAX_LANES)
+        return fail(LBM_FS_EINVAL, "config needs zb in 1..8, bulk_blocks >= 0, list_cells >= 1, lanes in 0..4%s");
     for (lbm_fs *t : b->tanks)
         if ((t->d[0].nz + c->zb - 1) / c->zb > 65535) return fail(LBM_FS_EINVAL, "zb too small for a tank%s");
     CK(cudaStreamSynchronize(b->st));
     b->zb = c->zb;
     b->bulk_blocks = c->bulk_blocks;
     b->list_cells = c->list_cells;
+    const int lanes = std::min<int>(c->lanes ? c->lanes : b->lanes, (int)b->tanks.size());
+    if (lanes != b->lanes) {
+        b->lanes = lanes;
+        make_chunks(b);
+    }
     b->built = false;
     b->drop_graphs();
     return LBM_FS_OK;
@@ -452,6 +514,7 @@ lbm_fs_status lbm_fs_batch_autotune(lbm_fs_batch *b, lbm_fs_batch_config_t *out)
         out->zb = b->zb;
         out->bulk_blocks = b->bulk_blocks;
         out->list_cells = b->list_cells;
+        out->lanes = b->lanes;
         out->bulk_ms = best;
     }
     return LBM_FS_OK;

@@ -68,7 +68,7 @@ class lbm_fs_stats_t(C.Structure):
 
 
 class lbm_fs_batch_config_t(C.Structure):
-    _fields_ = [("zb", C.c_int32), ("bulk_blocks", C.c_int32), ("list_cells", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("zb", C.c_int32), ("bulk_blocks", C.c_int32), ("list_cells", C.c_int32), ("lanes", C.c_int32),
                 ("bulk_ms", C.c_double)]
 
 
@@ -246,7 +246,7 @@ def lbm_fs_batch_sync(b):
 
 
 def _cfg_dict(c: lbm_fs_batch_config_t) -> dict:
-    return dict(zb=c.zb, bulk_blocks=c.bulk_blocks, list_cells=c.list_cells, bulk_ms=c.bulk_ms)
+    return dict(zb=c.zb, bulk_blocks=c.bulk_blocks, list_cells=c.list_cells, lanes=c.lanes, bulk_ms=c.bulk_ms)
 
 
 def lbm_fs_batch_autotune(b) -> dict:
@@ -261,8 +261,8 @@ def lbm_fs_batch_get_config(b) -> dict:
     return _cfg_dict(c)
 
 
-def lbm_fs_batch_set_config(b, zb: int, bulk_blocks: int, list_cells: int):
-    c = lbm_fs_batch_config_t(zb=int(zb), bulk_blocks=int(bulk_blocks), list_cells=int(list_cells))
+def lbm_fs_batch_set_config(b, zb: int, bulk_blocks: int, list_cells: int, lanes: int = 0):
+    c = lbm_fs_batch_config_t(zb=int(zb), bulk_blocks=int(bulk_blocks), list_cells=int(list_cells), lanes=int(lanes))
     _check(load().lbm_fs_batch_set_config(b, C.byref(c)), "lbm_fs_batch_set_config")
 
 
@@ -513,8 +513,8 @@ class Batch:
     def config(self) -> dict:
         return lbm_fs_batch_get_config(self.h)
 
-    def set_config(self, zb: int, bulk_blocks: int, list_cells: int):
-        lbm_fs_batch_set_config(self.h, zb, bulk_blocks, list_cells)
+    def set_config(self, zb: int, bulk_blocks: int, list_cells: int, lanes: int = 0):
+        lbm_fs_batch_set_config(self.h, zb, bulk_blocks, list_cells, lanes)
 
     def kernel_times(self, nsteps: int) -> dict:
         return lbm_fs_batch_kernel_times(self.h, nsteps)

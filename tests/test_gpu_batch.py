@@ -37,10 +37,13 @@ def _alone(sc, storage, steps):
     return g, b, st
 
 
-def _batched(scenes, storage, steps, use_graphs=True, autotune=False):
+def _batched(scenes, storage, steps, use_graphs=True, autotune=False, lanes=0):
     from paper_1201_0351_gb300 import lbm_fs
 
     bt = lbm_fs.Batch(scenes, storage=storage, use_graphs=use_graphs)
+    if lanes:
+        cfg = bt.config()
+        bt.set_config(cfg["zb"], cfg["bulk_blocks"], cfg["list_cells"], lanes)
     if autotune:
         cfg = bt.autotune()
         assert 1 <= cfg["zb"] <= 8 and cfg["bulk_ms"] > 0.0
@@ -69,12 +72,14 @@ def _same(a, b):
     assert abs(s1["wall_source"] - s2["wall_source"]) <= 1e-12 * max(1.0, abs(s2["wall_source"]))
 
 
-@pytest.mark.parametrize("storage", ["f64", "f16s"])
-def test_batch_equals_tanks_run_alone(storage):
+@pytest.mark.parametrize("storage,lanes", [("f64", 1), ("f16s", 1), ("f16s", 3)])
+def test_batch_equals_tanks_run_alone(storage, lanes):
+    """every kernel once per step for the tanks of each lane (concurrent
+    chains of launches), every tank bit for bit as alone"""
     scenes = _scenes()
     steps = 40
-    res, (launches, nsteps) = _batched(scenes, storage, steps)
-    assert nsteps == steps and launches == 16 * steps  # every kernel once per step for all tanks
+    res, (launches, nsteps) = _batched(scenes, storage, steps, lanes=lanes)
+    assert nsteps == steps and launches == 16 * lanes * steps
     for sc, r in zip(scenes, res):
         _same(r, _alone(sc, storage, steps))
 
@@ -118,7 +123,7 @@ def test_batch_of_more_than_64_tanks():
     scenes = [I.random_box_scene(12 + k % 5, 12 + k % 3, 12, seed=100 + k, nboxes=(k % 2), speed=0.02)
               for k in range(70)]
     steps = 12
-    res, (launches, _) = _batched(scenes, "f32", steps)
+    res, (launches, _) = _batched(scenes, "f32", steps, lanes=1)
     assert launches == 2 * 16 * steps
     for k in (0, 63, 64, 69):
         _same(res[k], _alone(scenes[k], "f32", steps))
@@ -133,9 +138,10 @@ def test_autotune_leaves_state_unchanged():
 
 
 def test_batch_graph_and_stream_agree():
+    """captured graphs and direct launches, both with two concurrent lanes"""
     scenes = _scenes()[:3]
-    a, _ = _batched(scenes, "f32", 15, use_graphs=True)
-    b, _ = _batched(scenes, "f32", 15, use_graphs=False)
+    a, _ = _batched(scenes, "f32", 15, use_graphs=True, lanes=2)
+    b, _ = _batched(scenes, "f32", 15, use_graphs=False, lanes=2)
     for x, y in zip(a, b):
         _same(x, y)
 
