@@ -170,7 +170,25 @@ def whole_job(ms_local: float, cells: int, steps: int, world: int, device: str =
     return ms, world * cells * steps / (ms * 1e-3) / 1e6
 
 
-def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=None):
+def stored_fp64_ops():
+    """Double-precision operations per liquid cell of the double-storage bulk
+    kernel, from the committed ncu capture; None when the kernel sources
+    changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_liquid_traffic.json")) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    r = rec.get("f64")
+    if not r or rec.get("kernel_source_sha256") != kernel_source_hash() or "dp_ops_per_liquid_cell" not in r:
+        return None
+    return r["dp_ops_per_liquid_cell"]
+
+
+def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=None, late=(0, 0)):
+    """Time `steps` steps after `warmup`; with late = (advance, k), also k
+    steps after advancing `advance` more (a window later in the job, when the
+    bodies move and the surface has folded)."""
     import torch
 
     from paper_1201_0351_gb300 import lbm_fs
@@ -198,6 +216,18 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
     st = sim.stats()
     launches = st["kernel_launches"] - launches0
     n_fluid1, n_liq1, n_if1 = fluid_counts(sim)
+    late_window = None
+    if late[0] > 0 and late[1] > 0:
+        sim.step(late[0])
+        sim.sync()
+        start.record(stream)
+        sim.step(late[1])
+        end.record(stream)
+        end.synchronize()
+        ml = start.elapsed_time(end)
+        n_all = sc.nx * sc.ny * sc.nz
+        late_window = dict(after_steps=warmup + steps + late[0], steps=late[1], ms_per_step=ml / late[1],
+                           mlups=n_all * late[1] / (ml * 1e-3) / 1e6, status=sim.stats()["status"])
     kt = sim.kernel_times(kernel_steps)
     sim.close()
     del sim
@@ -215,7 +245,8 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
                 liquid_ms=kt.get("liquid", float("nan")) / kernel_steps, liquid_bytes=liquid_bytes,
                 liquid_gbs=liquid_bytes / (kt.get("liquid", float("nan")) / kernel_steps * 1e-3) / 1e9,
                 kernel_share={k: v / total_k for k, v in kt.items() if total_k > 0},
-                launches=launches, status=st["status"], n_fluid=(n_liq + n_if), n_interface=n_if,
+                launches=launches, status=st["status"], n_fluid=(n_liq + n_if), n_interface=n_if, n_liquid=n_liq,
+                late_window=late_window,
                 mass_resid=(st["liquid_mass"] - st["mass0"] - (st["uncovered"] - st["covered"] - st["lost_excess"]
                                                                + st["wall_source"])) / st["mass0"])
 
@@ -395,6 +426,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-tank sweep")
     ap.add_argument("--batch-tanks", type=int, default=64, help="tanks of the batched sweep (small profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end run (default: the workload's job length)")
+    ap.add_argument("--late-advance", type=int, default=1000, help="steps run before the late timed window (0: none)")
+    ap.add_argument("--late-steps", type=int, default=20, help="steps of the late timed window")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     config = {"workload": "wave tank %dx%dx%d, %d free boxes 24x12x8, tau 0.52, g 1e-5" % (
@@ -433,12 +466,16 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sc = workload(args)
     clocks = ClockSampler(local)
-    main_run = run_storage(sc, "f32", args.steps, max(args.warmup, 3), 5, clocks=clocks, barrier=barrier)
+    main_run = run_storage(sc, "f32", args.steps, max(args.warmup, 3), 5, clocks=clocks, barrier=barrier,
+                           late=(args.late_advance, args.late_steps))
     variants = {}
     if not args.no_variants:
         variants["f16s"] = run_storage(sc, "f16s", args.steps, max(args.warmup, 3), 5, barrier=barrier)
         f64_steps = args.f64_steps or max(3, args.steps // 10)
         variants["f64"] = run_storage(sc, "f64", f64_steps, 3, 2, barrier=barrier)
+        from paper_1201_0351_gb300 import lbm_fs
+
+        fp64_rates = {name: lbm_fs.lbm_fs_fp64_rate(op) for op, name in ((0, "fma"), (1, "add"), (2, "mul"))}
     batch = None
     if not args.no_variants and not args.no_batch:
         from paper_1201_0351_gb300 import inputs
@@ -469,9 +506,26 @@ def main():
         "fluid_mlups": main_run["fluid_mlups"], "kernel_share": main_run["kernel_share"],
         "mass_drift_per_step": main_run["mass_resid"] / (args.steps + max(args.warmup, 3)),
         "variants": {k: {kk: v[kk] for kk in ("mlups", "ms_per_step", "liquid_gbs", "step_gbs", "launches",
-                                               "mass_resid")} | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k]}
+                                               "mass_resid", "liquid_ms", "liquid_bytes", "n_liquid")}
+                     | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k]}
                      for k, v in variants.items()},
     }
+    if main_run["late_window"] is not None:
+        line["late_window"] = main_run["late_window"]
+    if "f64" in variants:
+        # the double path is bound by double arithmetic (GB300's FP64 rate is
+        # 1/64 of its FP32 rate), not by memory: its bulk kernel's FP64
+        # operations per second against this GPU's measured add rate (the
+        # unit is built without fused multiply-add: adds and multiplies)
+        v = variants["f64"]
+        ops = stored_fp64_ops()
+        achieved = None if ops is None else ops * v["n_liquid"] / (v["liquid_ms"] * 1e-3)
+        line["variants"]["f64"]["roofline"] = {
+            "bound": "alu", "kernel": "k_liquid<0>", "unit": "FP64 op/s", "achieved": achieved,
+            "peak": fp64_rates["add"], "frac": None if achieved is None else achieved / fp64_rates["add"],
+            "peak_source": "measured in this run: lbm_fs_fp64_rate (independent add chains on every SM)",
+            "rates_measured": fp64_rates, "ops_per_liquid_cell": ops,
+            "ops_source": "ncu sass thread instructions dadd + dmul + dfma of one launch (profiles/k_liquid_traffic.json)"}
     if batch is not None:
         line["batch"] = {
             "workload": "%d tanks of edge 48..112 (seeded), heeled boxes, FP16-shifted storage, one launch per " % batch["tanks"] +

@@ -314,7 +314,9 @@ lbm_fs_status lbm_fs_batch_sync(lbm_fs_batch *b);
  *   lanes       groups of tanks (of about equal cell count) whose step
  *               launches form independent chains that the GPU runs side by
  *               side, one group's short list kernels beside another's bulk
- *               kernel (1..4; 0 keeps the current value; default 2);
+ *               kernel (1..4; 0 keeps the current value; default 1: on the
+ *               64-tank sweep 2 to 4 lanes measured no faster, the bulk
+ *               kernel filling every SM);
  *   bulk_ms     (autotune output) time of one bulk launch with this setting. */
 typedef struct {
     int32_t zb;
@@ -345,6 +347,16 @@ lbm_fs_status lbm_fs_batch_launches(lbm_fs_batch *b, int64_t *launches, int64_t 
 
 const char *lbm_fs_last_error_string(void);
 int32_t lbm_fs_version(void);
+
+/* Measurement helper (no counterpart in the paper): the rate at which this
+ * GPU executes one double-precision operation, op 0 fused multiply-add, 1 add,
+ * 2 multiply, in operations (thread instructions) per second, from
+ * independent chains on every SM timed with CUDA events on `stream` (NULL =
+ * legacy default stream).  The double-storage path is bound by this rate
+ * rather than by memory.  iters sets the chain length (about 2^20 gives a few
+ * milliseconds).  Synchronises; allocates nothing; bad arguments give
+ * LBM_FS_EINVAL, a failed launch LBM_FS_ECUDA. */
+lbm_fs_status lbm_fs_fp64_rate(int32_t op, int32_t iters, double *ops_per_s, void *stream);
 
 /* Liquid mass without allocating: sum over liquid and interface cells of the
  * per-cell mass, for callers that cannot allocate device memory (a host that

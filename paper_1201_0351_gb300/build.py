@@ -1,7 +1,8 @@
 """Builds libgb300_lbmfs.so (sm_103a) in-tree with nvcc.
 
 The translation units compile in parallel: the host API, the batched form,
-one kernel unit per population storage and the allocation-free reduction.  The double-precision unit is compiled with
+one kernel unit per population storage, the allocation-free reduction
+and the measurement helper.  The double-precision unit is compiled with
 -fmad=false (no fused multiply-add) so that it rounds every operation exactly
 as the plain CPU restatement of the method does.
 """
@@ -28,6 +29,7 @@ UNITS = {
     "kernels_f32.cu": [],
     "kernels_f16s.cu": [],
     "lbmfs_noalloc.cu": [],
+    "lbmfs_probe.cu": [],
 }
 
 

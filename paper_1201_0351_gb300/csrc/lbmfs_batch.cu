@@ -23,7 +23,7 @@ namespace {
 
 constexpr int ZB_DEFAULT = 4;
 constexpr int LIST_CELLS_DEFAULT = 512;
-constexpr int LANES_DEFAULT = 2;
+constexpr int LANES_DEFAULT = 1;
 
 constexpr int MAX_LANES = 4;
 

@@ -78,7 +78,7 @@ EXPORTS = ("lbm_fs_create", "lbm_fs_destroy", "lbm_fs_add_box", "lbm_fs_step", "
            "lbm_fs_version", "lbm_fs_liquid_mass_noalloc", "lbm_fs_noalloc_last_error_string",
            "lbm_fs_batch_create", "lbm_fs_batch_destroy", "lbm_fs_batch_tank", "lbm_fs_batch_step",
            "lbm_fs_batch_sync", "lbm_fs_batch_autotune", "lbm_fs_batch_set_config", "lbm_fs_batch_get_config",
-           "lbm_fs_batch_kernel_times", "lbm_fs_batch_launches")
+           "lbm_fs_batch_kernel_times", "lbm_fs_batch_launches", "lbm_fs_fp64_rate")
 
 _lib = None
 
@@ -131,6 +131,7 @@ def load(build_if_needed: bool = True):
     lib.lbm_fs_batch_get_config.argtypes = [P, CFG]
     lib.lbm_fs_batch_kernel_times.argtypes = [P, I32, D, C.POINTER(C.c_char_p), I32, C.POINTER(I32)]
     lib.lbm_fs_batch_launches.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.lbm_fs_fp64_rate.argtypes = [I32, I32, D, P]
     for name in EXPORTS:
         if name not in ("lbm_fs_last_error_string", "lbm_fs_version", "lbm_fs_noalloc_last_error_string"):
             getattr(lib, name).restype = C.c_int
@@ -279,6 +280,16 @@ def lbm_fs_batch_launches(b):
     n, st = C.c_int64(0), C.c_int64(0)
     _check(load().lbm_fs_batch_launches(b, C.byref(n), C.byref(st)), "lbm_fs_batch_launches")
     return n.value, st.value
+
+
+def lbm_fs_fp64_rate(op: int, iters: int = 1 << 20, stream: int = 0) -> float:
+    """Double-precision operations per second of this GPU (op 0 FMA, 1 add,
+    2 multiply)."""
+    r = C.c_double(0.0)
+    code = load().lbm_fs_fp64_rate(int(op), int(iters), C.byref(r), C.c_void_p(stream) if stream else None)
+    if code != LBM_FS_OK:
+        raise LbmFsError(code, "lbm_fs_fp64_rate", "probe launch failed")
+    return r.value
 
 
 # ------------------------------------------------------------ convenience
