@@ -77,3 +77,30 @@ def test_floating_cubes_reach_stable_heels():
     assert np.all(np.abs(mean - np.array(expect)) <= 2.0), (mean, expect)
     # the 0.5 box left its unstable upright start for good
     assert roll[-8:, 1].min() > 40.0, roll[:, 1]
+
+
+def test_floating_cubes_free_rotation_fp64():
+    """free rotation in all three axes (the double path, which equals the
+    oracle bit for bit, so the run is reproducible): the boxes roll about
+    their long axis to the same stable heels, within 2 deg over the last
+    8000 of 24000 steps; the tilt of the long axis (yaw and pitch, which
+    nothing restores but the walls) is printed"""
+    from paper_1201_0351_gb300 import lbm_fs
+    from floating import stable_heel_compressible
+
+    sc = I.floating_cubes(free_rotation=True, damping=0.01)
+    sim = lbm_fs.Simulation(sc, storage="f64")
+    roll, tilt = [], []
+    for _ in range(24):
+        sim.step(1000)
+        qs = [sim.body(k)["quat"] for k in range(3)]
+        roll.append([_roll(q) for q in qs])
+        tilt.append([_tilt(q) for q in qs])
+    st = sim.stats()
+    sim.close()
+    roll = np.array(roll)
+    expect = [stable_heel_compressible(b.density_ratio, 16.0, 7.5e-4) for b in sc.boxes]
+    mean = roll[-8:].mean(axis=0)
+    print("roll every 1000 steps", roll.round(2).tolist(), "tilt", np.array(tilt).round(1).tolist(), "expected", expect)
+    assert st["status"] == 0
+    assert np.all(np.abs(mean - np.array(expect)) <= 2.0), (mean, expect)
