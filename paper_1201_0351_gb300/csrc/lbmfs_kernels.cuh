@@ -2804,48 +2804,29 @@ __global__ void k_read_fields(Dev d, unsigned mask, uint8_t *flags, double *fill
 // table), each as the block of its tank's own grid that the entry names, with
 // the block size of the single-tank launch.  The per-cell work is the
 // single-tank kernels' own code.
-#ifndef LBMFS_BATCH_DEV_SMEM
-#define LBMFS_BATCH_DEV_SMEM 0  // tuning knob: the bulk body reads its tank's descriptor from shared memory
-#endif
 template <class K>
 __global__ void __launch_bounds__(K::THREADS, K::MINB)
     k_batch(const __grid_constant__ TankSet ts, const Tile *__restrict__ table, unsigned n, int zb) {
-    if constexpr (K::STAGE_DEV) {
-        // the tank's descriptor copied once per entry by the block's threads
-        // (parallel reads of the parameter space instead of a chain of
-        // dependent ones), then read from shared memory
-        __shared__ __align__(16) unsigned long long sd[(sizeof(Dev) + 7) / 8];
-        for (unsigned t = blockIdx.x; t < n; t += gridDim.x) {
-            const Tile e = table[t];
-            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&ts.d[e.tank]);
-            for (unsigned k = threadIdx.x; k < (sizeof(Dev) + 7) / 8; k += blockDim.x) sd[k] = src[k];
-            __syncthreads();
-            const VB vb{e.x, e.y, e.z, e.nx, e.ny, e.nz};
-            K::run(*reinterpret_cast<const Dev *>(sd), vb, zb);
-            __syncthreads();
-        }
-    } else {
-        for (unsigned t = blockIdx.x; t < n; t += gridDim.x) {
-            const Tile e = table[t];
-            const VB vb{e.x, e.y, e.z, e.nx, e.ny, e.nz};
-            K::run(ts.d[e.tank], vb, zb);
-            // the next entry's body reuses this one's shared memory; bodies
-            // without shared memory let a block's warps move on independently
-            if constexpr (K::SMEM) __syncthreads();
-        }
+    for (unsigned t = blockIdx.x; t < n; t += gridDim.x) {
+        const Tile e = table[t];
+        const VB vb{e.x, e.y, e.z, e.nx, e.ny, e.nz};
+        K::run(ts.d[e.tank], vb, zb);
+        // the next entry's body reuses this one's shared memory; bodies
+        // without shared memory let a block's warps move on independently
+        if constexpr (K::SMEM) __syncthreads();
     }
 }
 
 #define LBMFS_BATCH_BODY_SM(NAME, THR, MB, SM, CALL)                                          \
     struct NAME {                                                                              \
         static constexpr int THREADS = THR, MINB = MB;                                         \
-        static constexpr bool SMEM = SM, STAGE_DEV = false;                                    \
+        static constexpr bool SMEM = SM;                                                       \
         static __device__ __forceinline__ void run(const Dev &d, const VB &vb, int zb) { CALL; } \
     };
 #define LBMFS_BATCH_BODY(NAME, THR, MB, CALL) LBMFS_BATCH_BODY_SM(NAME, THR, MB, false, CALL)
 struct BkReset {
     static constexpr int THREADS = 32, MINB = 1;
-    static constexpr bool SMEM = false, STAGE_DEV = false;
+    static constexpr bool SMEM = false;
     static __device__ __forceinline__ void run(const Dev &d, const VB &, int) {
         if (threadIdx.x < WL_COUNT) d.cnt[threadIdx.x] = 0;
     }
@@ -2856,7 +2837,7 @@ template <int S, int ZB>
 struct BkLiquid {
     static constexpr int THREADS = BULK_THREADS;
     static constexpr int MINB = S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB);
-    static constexpr bool SMEM = false, STAGE_DEV = LBMFS_BATCH_DEV_SMEM != 0;
+    static constexpr bool SMEM = false;
     static __device__ __forceinline__ void run(const Dev &d, const VB &vb, int zb) { bulk_body<S, ZB>(d, vb, zb); }
 };
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
