@@ -507,7 +507,8 @@ def main():
         "mass_drift_per_step": main_run["mass_resid"] / (args.steps + max(args.warmup, 3)),
         "variants": {k: {kk: v[kk] for kk in ("mlups", "ms_per_step", "liquid_gbs", "step_gbs", "launches",
                                                "mass_resid", "liquid_ms", "liquid_bytes", "n_liquid")}
-                     | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k]}
+                     | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k],
+                        "traffic": stored_traffic(k, v["liquid_bytes"])}
                      for k, v in variants.items()},
     }
     if main_run["late_window"] is not None:

@@ -2834,12 +2834,8 @@ struct BkReset {
 template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MINB, true, forces_body<S>(d, vb))
 // one instantiation per z-planes-per-tile choice (the column loop unrolled to it)
 template <int S, int ZB>
-struct BkLiquid {
-    static constexpr int THREADS = BULK_THREADS;
-    static constexpr int MINB = S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB);
-    static constexpr bool SMEM = false;
-    static __device__ __forceinline__ void run(const Dev &d, const VB &vb, int zb) { bulk_body<S, ZB>(d, vb, zb); }
-};
+LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB),
+                 (bulk_body<S, ZB>(d, vb, zb)))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))

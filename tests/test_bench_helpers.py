@@ -30,4 +30,18 @@ def test_stored_traffic_is_scaled_or_withheld():
         assert abs(t - 2.0 * r["dram_bytes"]) <= 1e-9 * t
     else:
         assert t is None
-    assert bench.stored_traffic("f64", 1.0) is None
+    assert bench.stored_traffic("bf16", 1.0) is None  # no capture of that storage
+
+
+def test_stored_fp64_ops_follow_the_capture():
+    """The double path's operations per liquid cell come from the committed
+    capture while it belongs to the current kernel code."""
+    with open(os.path.join(bench.ROOT, "profiles", "k_liquid_traffic.json")) as fh:
+        rec = json.load(fh)
+    ops = bench.stored_fp64_ops()
+    if rec["kernel_source_sha256"] == bench.kernel_source_hash():
+        r = rec["f64"]
+        assert ops == r["dp_ops_per_liquid_cell"]
+        assert abs(r["dp_ops"] / r["liquid_cells"] - ops) < 0.01
+    else:
+        assert ops is None
