@@ -282,7 +282,7 @@ def lbm_fs_batch_launches(b):
     return n.value, st.value
 
 
-def lbm_fs_fp64_rate(op: int, iters: int = 1 << 20, stream: int = 0) -> float:
+def lbm_fs_fp64_rate(op: int, iters: int = 1 << 16, stream: int = 0) -> float:
     """Double-precision operations per second of this GPU (op 0 FMA, 1 add,
     2 multiply)."""
     r = C.c_double(0.0)
