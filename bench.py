@@ -197,7 +197,8 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
     sim.step(warmup)
     sim.sync()
     n_fluid0, n_liq0, n_if0 = fluid_counts(sim)
-    launches0 = sim.stats()["kernel_launches"]
+    st0 = sim.stats()
+    launches0, n_gen0 = st0["kernel_launches"], st0["n_general"]
     stream = sim.stream
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if barrier:
@@ -235,10 +236,11 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
     n = sc.nx * sc.ny * sc.nz
     n_liq = 0.5 * (n_liq0 + n_liq1)
     n_if = 0.5 * (n_if0 + n_if1)
+    n_gen = 0.5 * (n_gen0 + st["n_general"])  # liquid cells stepped by the general-gather kernel
     b_fluid = BYTES_PER_FLUID[storage]
     # one flag byte per fluid cell (tiles of gas above the fluid are never read)
     step_bytes = (n_liq + n_if) * (b_fluid + 1) + n_if * 24
-    liquid_bytes = n_liq * b_fluid + (n_liq + n_if) * 1
+    liquid_bytes = (n_liq - n_gen) * b_fluid + (n_liq + n_if) * 1
     total_k = sum(kt.values())
     return dict(storage=storage, ms_total=ms, ms_per_step=ms / steps, mlups=n * steps / (ms * 1e-3) / 1e6,
                 fluid_mlups=(n_liq + n_if) * steps / (ms * 1e-3) / 1e6, step_gbs=step_bytes / (ms / steps * 1e-3) / 1e9,
@@ -246,7 +248,7 @@ def run_storage(sc, storage, steps, warmup, kernel_steps, clocks=None, barrier=N
                 liquid_gbs=liquid_bytes / (kt.get("liquid", float("nan")) / kernel_steps * 1e-3) / 1e9,
                 kernel_share={k: v / total_k for k, v in kt.items() if total_k > 0},
                 launches=launches, status=st["status"], n_fluid=(n_liq + n_if), n_interface=n_if, n_liquid=n_liq,
-                late_window=late_window,
+                n_general=n_gen, late_window=late_window,
                 mass_resid=(st["liquid_mass"] - st["mass0"] - (st["uncovered"] - st["covered"] - st["lost_excess"]
                                                                + st["wall_source"])) / st["mass0"])
 
@@ -268,14 +270,15 @@ def run_batch(scenes, storage, steps, warmup, kernel_steps, separate_steps=20, b
     bt.sync()
 
     def counts():
-        liq = itf = 0
+        liq = itf = gen = 0
         for t in bt.tanks:
             fl = t.flags()
             liq += int((fl == 1).sum())
             itf += int((fl == 2).sum())
-        return liq, itf
+            gen += int(t.stats()["n_general"])
+        return liq, itf, gen
 
-    liq0, if0 = counts()
+    liq0, if0, gen0 = counts()
     launches0, _ = bt.launches()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if barrier:
@@ -289,17 +292,17 @@ def run_batch(scenes, storage, steps, warmup, kernel_steps, separate_steps=20, b
         barrier()
     ms = start.elapsed_time(end)
     launches = bt.launches()[0] - launches0
-    liq1, if1 = counts()
+    liq1, if1, gen1 = counts()
     kt = bt.kernel_times(kernel_steps)
     bt.sync()
     cells = bt.cells
     bt.close()
     del bt
     torch.cuda.empty_cache()
-    n_liq, n_if = 0.5 * (liq0 + liq1), 0.5 * (if0 + if1)
+    n_liq, n_if, n_gen = 0.5 * (liq0 + liq1), 0.5 * (if0 + if1), 0.5 * (gen0 + gen1)
     b_fluid = BYTES_PER_FLUID[storage]
     step_bytes = (n_liq + n_if) * (b_fluid + 1) + n_if * 24
-    liquid_bytes = n_liq * b_fluid + (n_liq + n_if) * 1
+    liquid_bytes = (n_liq - n_gen) * b_fluid + (n_liq + n_if) * 1
     liquid_ms = kt["liquid"] / kernel_steps
     # the same tanks as separate handles (each with its own captured graphs)
     ms_sep = None
@@ -506,7 +509,7 @@ def main():
         "fluid_mlups": main_run["fluid_mlups"], "kernel_share": main_run["kernel_share"],
         "mass_drift_per_step": main_run["mass_resid"] / (args.steps + max(args.warmup, 3)),
         "variants": {k: {kk: v[kk] for kk in ("mlups", "ms_per_step", "liquid_gbs", "step_gbs", "launches",
-                                               "mass_resid", "liquid_ms", "liquid_bytes", "n_liquid")}
+                                               "mass_resid", "liquid_ms", "liquid_bytes", "n_liquid", "n_general")}
                      | {"frac": v["liquid_gbs"] / hbm, "dtype": DTYPE[k],
                         "traffic": stored_traffic(k, v["liquid_bytes"])}
                      for k, v in variants.items()},
@@ -520,7 +523,7 @@ def main():
         # unit is built without fused multiply-add: adds and multiplies)
         v = variants["f64"]
         ops = stored_fp64_ops()
-        achieved = None if ops is None else ops * v["n_liquid"] / (v["liquid_ms"] * 1e-3)
+        achieved = None if ops is None else ops * (v["n_liquid"] - v["n_general"]) / (v["liquid_ms"] * 1e-3)
         line["variants"]["f64"]["roofline"] = {
             "bound": "alu", "kernel": "k_liquid<0>", "unit": "FP64 op/s", "achieved": achieved,
             "peak": fp64_rates["add"], "frac": None if achieved is None else achieved / fp64_rates["add"],

@@ -185,6 +185,9 @@ typedef struct {
                               6 w_q rho (c_q . u_w) of Eq. noslip.  Ledger identity:
                               liquid_mass = mass0 + uncovered - covered
                               - lost_excess + wall_source (to rounding) */
+    int64_t n_general;     /* liquid cells of the last step with an obstacle among
+                              their neighbours or on a face with moving walls
+                              (stepped by the general-gather kernel) */
 } lbm_fs_stats_t;
 
 /* field selectors for lbm_fs_read_fields; dst[k] is the buffer for bit k.

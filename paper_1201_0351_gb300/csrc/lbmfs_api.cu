@@ -509,6 +509,7 @@ lbm_fs_status lbm_fs_stats(lbm_fs *h, lbm_fs_stats_t *out) {
     out->status = status;
     out->kernel_launches = h->launches;
     out->wall_source = lg[LG_WALL];
+    out->n_general = cnt[WL_GEN];
     return read_status(h);
 }
 

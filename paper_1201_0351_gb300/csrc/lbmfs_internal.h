@@ -40,7 +40,7 @@ enum : uint32_t { ST_LIQUID_GAS = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4, ST_TIMEO
 constexpr int ZTOP_MARGIN = 4;
 
 // worklists
-enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_COUNT };
+enum { WL_IFACE = 0, WL_FILLED, WL_EMPTIED, WL_NEWG, WL_NEWL, WL_RECV, WL_PEND, WL_COVER, WL_GEN, WL_COUNT };
 // ledger slots (double)
 enum { LG_COVERED = 0, LG_UNCOVERED, LG_LOST, LG_MASS0, LG_MASS, LG_WALL, LG_COUNT };
 

@@ -547,20 +547,31 @@ __device__ __forceinline__ double link_cuw(const Dev &d, const Body &b, int x, i
 }
 
 // the same in float for the float storages: the body state is rounded once
-// (positions relative to the body centre stay well inside float precision)
-__device__ __forceinline__ float link_cuw_f(const Dev &d, const Body &b, int x, int y, int z, int q) {
+// (positions relative to the body centre stay well inside float precision).
+// BodyF holds what a cell's links share: the cell's offset from the body
+// centre, rounded from double, and the body's velocities.
+struct BodyF {
+    float r0[3], v[3], w[3];
+};
+__device__ __forceinline__ BodyF body_f(const Body &b, int x, int y, int z) {
+    return BodyF{{(float)(x - b.o[0]), (float)(y - b.o[1]), (float)(z - b.o[2])},
+                 {(float)b.v[0], (float)b.v[1], (float)b.v[2]},
+                 {(float)b.w[0], (float)b.w[1], (float)b.w[2]}};
+}
+__device__ __forceinline__ float link_cuw_f(const Dev &d, const BodyF &b, int q) {
     const int qb = opp(q);
-    float r[3] = {(float)(x - b.o[0]) + (0.5f + 0.5f * cx(qb)), (float)(y - b.o[1]) + (0.5f + 0.5f * cy(qb)),
-                  (float)(z - b.o[2]) + (0.5f + 0.5f * cz(qb))};
+    float r[3] = {b.r0[0] + (0.5f + 0.5f * cx(qb)), b.r0[1] + (0.5f + 0.5f * cy(qb)), b.r0[2] + (0.5f + 0.5f * cz(qb))};
     const int nn[3] = {d.nx, d.ny, d.nz};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         if (d.periodic & (1u << k)) r[k] -= (float)nn[k] * floorf(r[k] / (float)nn[k] + 0.5f);
-    const float w0 = (float)b.w[0], w1 = (float)b.w[1], w2 = (float)b.w[2];
-    const float u0 = (float)b.v[0] + (w1 * r[2] - w2 * r[1]);
-    const float u1 = (float)b.v[1] + (w2 * r[0] - w0 * r[2]);
-    const float u2 = (float)b.v[2] + (w0 * r[1] - w1 * r[0]);
+    const float u0 = b.v[0] + (b.w[1] * r[2] - b.w[2] * r[1]);
+    const float u1 = b.v[1] + (b.w[2] * r[0] - b.w[0] * r[2]);
+    const float u2 = b.v[2] + (b.w[0] * r[1] - b.w[1] * r[0]);
     return (cx(q) * u0 + cy(q) * u1) + cz(q) * u2;
+}
+__device__ __forceinline__ float link_cuw_f(const Dev &d, const Body &b, int x, int y, int z, int q) {
+    return link_cuw_f(d, body_f(b, x, y, z), q);
 }
 
 // ------------------------------------------------- double arithmetic (Sec. 2.1)
@@ -1329,41 +1340,6 @@ __global__ void __launch_bounds__(256, S == 0 ? 2 : LBMFS_FORCE_MINB) k_forces(c
     forces_body<S>(d, vb_own());
 }
 
-// Eq. noslip for the link (x, q) whose source cell si (class ns) is a wall or
-// an obstacle: f'_q = f*_qbar + 6 w_q rho_x (c_q . u_w); u_w = 0 at walls.
-// Returns f'_q and the mass the moving wall adds to the cell (the caller sums
-// it per cell for the ledger).  Double arithmetic for the FP64 storage; float
-// for the float storages, whose populations are float anyway (GB300's FP64
-// rate is 1/64 of its FP32 rate).  Kept out of line so that the bulk kernel's
-// populations stay in registers.
-template <class R> struct Bounce {
-    R f, src;
-};
-template <int S>
-__device__ __noinline__ Bounce<typename Sto<S>::R> bounce_back(const Dev &d, int q, long long si, int ns, long long i,
-                                                               int x, int y, int z) {
-    using R = typename Sto<S>::R;
-    const int qb = opp(q);
-    const R own = Sto<S>::ld(d.fsrc, qb, i, d.N);
-    if (ns == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
-    if (ns != CL_O && !(ns == CL_WALL && d.walls_move)) return Bounce<R>{own, R(0)};
-    if constexpr (S == 0) {
-        const double cuw = ns == CL_O ? link_cuw(d, d.bodies[d.bid[si]], x, y, z, q) : wall_cuw(d, x, y, z, q);
-        if (cuw == 0.0) return Bounce<R>{own, 0.0};
-        const double rho_x = cell_density<S>(d, d.fsrc, i);
-        const double src = ((6.0 * wd(q)) * rho_x) * cuw;
-        return Bounce<R>{own + src, src};
-    } else {
-        const float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q) : (float)wall_cuw(d, x, y, z, q);
-        if (cuw == 0.0f) return Bounce<R>{own, 0.0f};
-        float dr = 0.0f;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) dr += Sto<S>::ld(d.fsrc, k, i, d.N);
-        const float src = ((6.0f * wf(q)) * (1.0f + dr)) * cuw;
-        return Bounce<R>{own + src, src};
-    }
-}
-
 // ---- C1 + C2 for liquid cells (Sec. 2.1 Eqs. stream, lbgk, forceterm;
 // Sec. 2.3 Eq. noslip); interface cells are listed for k_interface
 template <int S, int ZBMAX>
@@ -1432,39 +1408,136 @@ template <int S> __device__ __forceinline__ void to_raw(typename Sto<S>::R *fp) 
 
 // populations arriving at a liquid cell with an obstacle or wall neighbour, or
 // on a periodic seam: per-direction source classes, bounce-back where the
-// source is solid
+// source is solid (Eq. noslip), 6 w_q rho_x c_q.u_w added where the solid
+// moves.  Three rounds of independent loads: the 18 source classes with the
+// cell's own 19 populations; the pulled populations with the body ids of the
+// obstacle sources; the state of the body (one body for all links when they
+// share it, the common case; per link otherwise).  rho_x, in double for the
+// FP64 storage and in float for the float storages, sums the own populations
+// in q order.  Returns the mass the moving links add to the cell (for the
+// ledger).
 template <int S>
-__device__ __forceinline__ void gather_general(const Dev &d, int x, int y, int z, long long i,
-                                               typename Sto<S>::R *fp) {
+__device__ __forceinline__ double gather_general(const Dev &d, int x, int y, int z, long long i,
+                                                 typename Sto<S>::R *fp) {
     using P = Sto<S>;
-    typename P::R wall = 0;
+    using R = typename P::R;
+    const long long N = d.N;
+    long long src[Q];
+    int ns[Q];
+    R own[Q];
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-        long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-        int ns = cls(d, si);
-        if (ns == CL_L || ns == CL_I) {
-            fp[q] = P::ld(d.fsrc, q, si, d.N);
-        } else {
-            const auto b = bounce_back<S>(d, q, si, ns, i, x, y, z);
-            fp[q] = b.f;
-            wall += b.src;
+        src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+        ns[q] = src[q] < 0 ? CL_WALL : clsv(d, src[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) own[q] = P::ld(d.fsrc, q, i, N);
+    unsigned moving = 0, obst = 0;  // directions with a moving solid source / an obstacle source
+    int bq[Q];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const bool pull = ns[q] == CL_L || ns[q] == CL_I;
+        fp[q] = pull ? P::ld(d.fsrc, q, src[q], N) : own[opp(q)];
+        bq[q] = ns[q] == CL_O ? d.bid[src[q]] : -1;
+        if (ns[q] == CL_O) obst |= 1u << q;
+        if (ns[q] == CL_O || (ns[q] == CL_WALL && d.walls_move)) moving |= 1u << q;
+        if (ns[q] == CL_G) atomicOr(d.status, ST_LIQUID_GAS);
+    }
+    fp[0] = own[0];
+    if (!moving) return 0.0;
+    int b0 = -1;
+    bool one = true;  // every obstacle link belongs to body b0
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+        if (obst & (1u << q)) {
+            if (b0 < 0) b0 = bq[q];
+            one = one && bq[q] == b0;
+        }
+    R wall = 0;
+    if constexpr (S == 0) {
+        double rho_x = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) rho_x += own[q];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (!(moving & (1u << q))) continue;
+            const double cuw = (obst & (1u << q)) ? link_cuw(d, d.bodies[one ? b0 : bq[q]], x, y, z, q)
+                                                  : wall_cuw(d, x, y, z, q);
+            if (cuw == 0.0) continue;
+            const double srcm = ((6.0 * wd(q)) * rho_x) * cuw;
+            fp[q] = fp[q] + srcm;
+            wall += srcm;
+        }
+    } else {
+        float dr = 0.0f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dr += own[k];
+        const float rho_x = 1.0f + dr;
+        BodyF bf0;
+        if (b0 >= 0) bf0 = body_f(d.bodies[b0], x, y, z);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (!(moving & (1u << q))) continue;
+            const float cuw = (obst & (1u << q))
+                                  ? (one ? link_cuw_f(d, bf0, q) : link_cuw_f(d, d.bodies[bq[q]], x, y, z, q))
+                                  : (float)wall_cuw(d, x, y, z, q);
+            if (cuw == 0.0f) continue;
+            const float srcm = ((6.0f * wf(q)) * rho_x) * cuw;
+            fp[q] = fp[q] + srcm;
+            wall += srcm;
         }
     }
-    fp[0] = P::ld(d.fsrc, 0, i, d.N);
-    if (wall != 0) atomicAdd(&d.ledger[LG_WALL], (double)wall);  // mass the moving walls added to the cell
+    return (double)wall;
 }
 
 template <int S>
-__device__ __forceinline__ void liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
+__device__ __forceinline__ double liquid_cell_general(const Dev &d, int x, int y, int z, long long i) {
     typename Sto<S>::R fp[Q];
-    gather_general<S>(d, x, y, z, i, fp);
+    const double wall = gather_general<S>(d, x, y, z, i, fp);
     to_raw<S>(fp);
     collide_store<S>(d, fp, i);
+    return wall;
 }
 
-// One liquid cell (class byte c, coordinates x, y, z, index i): gather its
-// 18 arriving populations by the cheapest rule that holds for it, collide and
-// store.
+// C1 + C2 for the liquid cells the bulk kernel listed (an obstacle among the
+// neighbours, or a grid face with moving walls): the general gather, then the
+// collision.  They read the source grid and write their own cell of the
+// destination grid only, as the bulk kernel would have.
+// The mass the moving links add is summed per warp and goes to the ledger
+// with one atomic per warp (thousands of cells adding to one address would
+// queue on it).  Blocks of GEN_THREADS spread the few listed cells over many
+// SMs.
+constexpr int GEN_THREADS = 128;
+template <int S> __device__ __forceinline__ void general_body(const Dev &d, const VB &vb) {
+    double wacc = 0.0;
+    LIST_LOOP(WL_GEN, g) {
+        const long long i = d.list[WL_GEN][it_g];
+        int x, y, z;
+        if constexpr (S != 0) {
+            // the float storages hold N * 19 < 2^32 elements
+            const uint32_t i32 = (uint32_t)i, yz = i32 / (uint32_t)d.nx;
+            x = (int)(i32 - yz * (uint32_t)d.nx);
+            y = (int)(yz % (uint32_t)d.ny);
+            z = (int)(yz / (uint32_t)d.ny);
+        } else {
+            coords(d, i, x, y, z);
+        }
+        wacc += liquid_cell_general<S>(d, x, y, z, i);
+    }
+    if (__any_sync(0xffffffffu, wacc != 0.0)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) wacc += __shfl_xor_sync(0xffffffffu, wacc, off);
+        if ((threadIdx.x & 31) == 0 && wacc != 0.0) atomicAdd(&d.ledger[LG_WALL], wacc);
+    }
+}
+template <int S>
+__global__ void __launch_bounds__(GEN_THREADS, 1) k_general(const __grid_constant__ Dev d) {
+    general_body<S>(d, vb_own());
+}
+
+// One liquid cell (class byte c, coordinates x, y, z, index i; not a
+// general_cell): gather its 18 arriving populations by the cheapest rule that
+// holds for it, collide and store.
 template <int S>
 __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, int z, long long i) {
     using P = Sto<S>;
@@ -1492,7 +1565,7 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
                         : P::ldg_raw(d.fsrc, q, i - (cx(q) + cy(q) * sy + cz(q) * sz), N);
         }
         fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-    } else if (c == CL_L && !d.walls_move) {
+    } else {
         // on a face with periodic axes: pull across the seams, walls as above
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -1500,11 +1573,16 @@ __device__ __forceinline__ void liquid_one(const Dev &d, int c, int x, int y, in
             fp[q] = si >= 0 ? P::ldg_raw(d.fsrc, q, si, N) : P::ldg_raw(d.fsrc, opp(q), i, N);
         }
         fp[0] = P::ldg_raw(d.fsrc, 0, i, N);
-    } else {
-        gather_general<S>(d, x, y, z, i, fp);
-        to_raw<S>(fp);
     }
     collide_store<S>(d, fp, i);  // one copy of the collision in the kernel
+}
+// A liquid cell the bulk kernel leaves to k_general (class byte c): an
+// obstacle among its neighbours (the neighbour-obstacle bit), or a grid face
+// when the walls move.  Its class, body-id and body-state loads depend on one
+// another; in k_general they hold none of the bulk kernel's warps.
+__device__ __forceinline__ bool general_cell(const Dev &d, int c, int x, int y, int z) {
+    return (c & CL_MASK) == CL_L &&
+           (c != CL_L || (d.walls_move && !(x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1)));
 }
 
 // The cells (x, y, z0 .. z1-1) of one thread.  The flags of the whole column
@@ -1528,7 +1606,9 @@ __device__ __forceinline__ void liquid_column(const Dev &d, bool in, int x, int 
         const int c = (int)(fl & 0xff);
         fl >>= 8;
         wl_append(d, (c & CL_MASK) == CL_I, WL_IFACE, (uint32_t)i);
-        if ((c & CL_MASK) != CL_L) continue;
+        const bool gen = general_cell(d, c, x, y, z);
+        wl_append(d, gen, WL_GEN, (uint32_t)i);
+        if ((c & CL_MASK) != CL_L || gen) continue;
         liquid_one<S>(d, c, x, y, z, i);  // one copy of the collision in the kernel
     }
 }
@@ -1575,6 +1655,9 @@ __device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int
         const int c0 = (int)(fl[k] & 0xffu), c1 = (int)(fl[k] >> 8);
         wl_append(d, (c0 & CL_MASK) == CL_I, WL_IFACE, j);
         wl_append(d, (c1 & CL_MASK) == CL_I, WL_IFACE, j + 1);
+        const bool g0 = general_cell(d, c0, x0, y0, z), g1 = general_cell(d, c1, x0 + 1, y0, z);
+        wl_append(d, g0, WL_GEN, j);
+        wl_append(d, g1, WL_GEN, j + 1);
         if (pair_xy && c0 == CL_L && c1 == CL_L && z > 0 && z < d.nz - 1) {
             float2 fp[Q];
 #pragma unroll
@@ -1589,7 +1672,7 @@ __device__ __forceinline__ void liquid_body_pair(const Dev &d, const VB &vb, int
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const int c = h ? c1 : c0;
-                if ((c & CL_MASK) != CL_L) continue;
+                if ((c & CL_MASK) != CL_L || (h ? g1 : g0)) continue;
                 liquid_one<S>(d, c, x0 + h, y0, z, (long long)(j + h));
             }
         }
@@ -1684,7 +1767,8 @@ __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_pipe(D
             to_raw<S>(fp);
             collide_store<S>(d, fp, i);
         } else if ((fl_cur & CL_MASK) == CL_L) {
-            liquid_cell_general<S>(d, x, y, z, i);
+            const double w = liquid_cell_general<S>(d, x, y, z, i);
+            if (w != 0.0) atomicAdd(&d.ledger[LG_WALL], w);
         }
         fl_cur = fl_next;
         fl_next = fl_after;
@@ -1835,7 +1919,8 @@ __global__ void __launch_bounds__(BULK_THREADS, LBMFS_BULK_MINB) k_liquid_tma(De
             to_raw<S>(fp);
             collide_store<S>(d, fp, i);
         } else if ((c & CL_MASK) == CL_L) {
-            liquid_cell_general<S>(d, x, y, z, i);
+            const double w = liquid_cell_general<S>(d, x, y, z, i);
+            if (w != 0.0) atomicAdd(&d.ledger[LG_WALL], w);
         }
         fl_cur = fl_next;
         fl_next = fl_after;
@@ -1927,10 +2012,314 @@ __device__ __noinline__ float curvature_f(const Dev &d, int x, int y, int z, flo
     return 0.25f * div;
 }
 
-// ---- C1 + C2 for interface cells (Sec. 2.2): reconstruction, mass exchange
+// ---- C1 + C2 for interface cells of the float storages: three threads per
+// cell.  Member r of a cell's trio owns three pairs of opposite directions
+// (r = 0: W/E, TW/BE, TE/BW; r = 1: N/S, TN/BS, TS/BN; r = 2: T/B, NW/SE,
+// NE/SW), so the bounce-back, reconstruction and mass exchange of a link,
+// which pair q with qbar, stay inside one thread, and the first pair of
+// member r is the axis pair of component r of the normal.  Sums over all
+// directions (density, momentum, exchanged mass, the stored cell sum) are
+// formed per member and added as member 0 + member 1 + member 2 on all three
+// threads, so a trio agrees bit for bit.  Ten trios per warp; lanes 30 and 31
+// shadow the last trio and write nothing.
+
+// neighbour (x + dx, y + dy, z + dz) as a 32-bit cell index without
+// branches (periodic axes wrap); -1 beyond a wall
+__device__ __forceinline__ int nbr32(const Dev &d, int x, int y, int z, int dx, int dy, int dz) {
+    int px = x + dx, py = y + dy, pz = z + dz;
+    const bool ox = px < 0 || px >= d.nx, oy = py < 0 || py >= d.ny, oz = pz < 0 || pz >= d.nz;
+    px = px < 0 ? px + d.nx : (px >= d.nx ? px - d.nx : px);
+    py = py < 0 ? py + d.ny : (py >= d.ny ? py - d.ny : py);
+    pz = pz < 0 ? pz + d.nz : (pz >= d.nz ? pz - d.nz : pz);
+    const bool wall = (ox && !(d.periodic & 1u)) || (oy && !(d.periodic & 2u)) || (oz && !(d.periodic & 4u));
+    return wall ? -1 : px + d.nx * (py + d.ny * pz);
+}
+// moving population q >= 1 of cell j as a float deviation (no branch on q)
+template <int S> __device__ __forceinline__ float trio_ld(const void *g, int q, uint32_t j, long long N) {
+    if constexpr (S == 1) return __ldg(reinterpret_cast<const float *>(g) + ((long long)q * N + j));
+    else return __half2float(__ldg(Sto<2>::hp(g, N) + ((long long)(q - 1) * N + j))) * F16_INV_SCALE;
+}
+// store moving population q >= 1 of cell j; returns the value as stored
+template <int S> __device__ __forceinline__ float trio_st(void *g, int q, uint32_t j, long long N, float v) {
+    if constexpr (S == 1) {
+        pop_st(reinterpret_cast<float *>(g) + ((long long)q * N + j), v);
+        return v;
+    } else {
+        const __half h = __float2half_rn(v * F16_SCALE);
+        pop_st(const_cast<__half *>(Sto<2>::hp(g, N)) + ((long long)(q - 1) * N + j), h);
+        return __half2float(h) * F16_INV_SCALE;
+    }
+}
+__host__ __device__ constexpr int trio_q(int r, int k) {
+    return r == 0 ? (k == 0 ? 1 : (k == 1 ? 7 : 8)) : (r == 1 ? (k == 0 ? 3 : (k == 1 ? 9 : 10)) : (k == 0 ? 5 : (k == 1 ? 11 : 12)));
+}
+__host__ __device__ constexpr bool trio_ok() {
+    int seen = 0;
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) {
+            const int q = trio_q(r, k), b = opp(q);
+            if ((seen >> q) & 1 || (seen >> b) & 1) return false;
+            seen |= (1 << q) | (1 << b);
+            if ((k == 0) != (q <= 6)) return false;  // the first pair is the axis pair
+        }
+    return seen == (1 << Q) - 2 && trio_q(0, 0) == 1 && trio_q(1, 0) == 3 && trio_q(2, 0) == 5;
+}
+static_assert(trio_ok(), "trio pairs: each moving direction once, axis pair first");
+// the value f(q) for the first direction q of pair k of member r (three
+// compile-time constants, selected by r)
+template <int K, class F> __device__ __forceinline__ int trio_sel(int r, F f) {
+    return r == 0 ? f(trio_q(0, K)) : (r == 1 ? f(trio_q(1, K)) : f(trio_q(2, K)));
+}
+__device__ __forceinline__ float trio_sum(float v, int b3) {
+    const float a = __shfl_sync(0xffffffffu, v, b3), b = __shfl_sync(0xffffffffu, v, b3 + 1),
+                c = __shfl_sync(0xffffffffu, v, b3 + 2);
+    return (a + b) + c;
+}
+// f_eq(rho_g, u) - w for a direction of weight w with c.u = cu
+__device__ __forceinline__ float feq_dev_cu(float w, float cu, float usq, float drg) {
+    const float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
+    return w * (drg + s + drg * s);
+}
+
 template <int S>
-__device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
+__device__ __forceinline__ void interface_trio(const Dev &d, const VB &vb) {
     using P = Sto<S>;
+    const long long N = d.N;
+    const unsigned FULL = 0xffffffffu;
+    if (vb.x == 0 && threadIdx.x == 0) *d.ztop_rd = -1;
+    const int lane = threadIdx.x & 31;
+    const bool lane_ok = lane < 30;
+    const int g = lane_ok ? lane / 3 : 9;             // trio of the warp
+    const int r = lane_ok ? lane - 3 * g : lane - 30;  // member
+    const int b3 = 3 * g;
+    // pair k: first direction a = trio_q(r, k) with velocity e, second b = opp(a)
+    // with -e; sg = +1 when a is the pair member whose leading nonzero
+    // component is positive (the collision's split, see collide_store_v).
+    // Packed in one word per pair (a, b: 5 bits each; e + 1: 2 bits per
+    // component; sg > 0: 1 bit) to keep the loop's registers for the cells.
+    uint32_t pk[3];
+    const auto pack = [](int q) {
+        const bool pos = cx(q) > 0 || (cx(q) == 0 && (cy(q) > 0 || (cy(q) == 0 && cz(q) > 0)));
+        return q | (opp(q) << 5) | ((cx(q) + 1) << 10) | ((cy(q) + 1) << 12) | ((cz(q) + 1) << 14) | ((pos ? 1 : 0) << 16);
+    };
+    pk[0] = (uint32_t)trio_sel<0>(r, pack);
+    pk[1] = (uint32_t)trio_sel<1>(r, pack);
+    pk[2] = (uint32_t)trio_sel<2>(r, pack);
+#define TRIO_QA(k) ((int)(pk[k] & 31u))
+#define TRIO_QB(k) ((int)((pk[k] >> 5) & 31u))
+#define TRIO_EX(k) ((int)((pk[k] >> 10) & 3u) - 1)
+#define TRIO_EY(k) ((int)((pk[k] >> 12) & 3u) - 1)
+#define TRIO_EZ(k) ((int)((pk[k] >> 14) & 3u) - 1)
+#define TRIO_POS(k) ((pk[k] >> 16) & 1u)
+    const float ax = d.a_f[0], ay = d.a_f[1], az = d.a_f[2];
+    const uint32_t n = wl_count(d, WL_IFACE);
+    const uint32_t wpb = blockDim.x >> 5;
+    for (uint32_t w0 = (vb.x * wpb + (threadIdx.x >> 5)) * 10u; w0 < n; w0 += vb.nx * wpb * 10u) {
+        const uint32_t it = w0 + (uint32_t)g;
+        const bool valid = lane_ok && it < n;
+        const long long i = d.list[WL_IFACE][valid ? it : w0];
+        const uint32_t i32 = (uint32_t)i;  // the float storages hold N * 19 < 2^32 elements
+        const int x = (int)(i32 % (uint32_t)d.nx);
+        const uint32_t yz = i32 / (uint32_t)d.nx;
+        const int y = (int)(yz % (uint32_t)d.ny), z = (int)(yz / (uint32_t)d.ny);
+        // every load of the cell in one round, independent of the neighbour
+        // classes: a source beyond a wall reads the cell itself (unused), so
+        // no load waits on another and none sits behind a branch
+        const float phx = (float)__ldg(d.phisrc + i);
+        float foa[3], fob[3], pa[3], pb[3];
+        double ha[3], hb[3];
+        int sa[3], sb[3], ca[3], cb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            foa[k] = trio_ld<S>(d.fsrc, TRIO_QA(k), i32, N);
+            fob[k] = trio_ld<S>(d.fsrc, TRIO_QB(k), i32, N);
+            sa[k] = nbr32(d, x, y, z, -TRIO_EX(k), -TRIO_EY(k), -TRIO_EZ(k));
+            sb[k] = nbr32(d, x, y, z, TRIO_EX(k), TRIO_EY(k), TRIO_EZ(k));
+            const uint32_t la = sa[k] < 0 ? i32 : (uint32_t)sa[k], lb = sb[k] < 0 ? i32 : (uint32_t)sb[k];
+            ca[k] = __ldg(d.flags + la) & CL_MASK;
+            cb[k] = __ldg(d.flags + lb) & CL_MASK;
+            pa[k] = trio_ld<S>(d.fsrc, TRIO_QA(k), la, N);
+            pb[k] = trio_ld<S>(d.fsrc, TRIO_QB(k), lb, N);
+            ha[k] = __ldg(d.phisrc + la);
+            hb[k] = __ldg(d.phisrc + lb);
+        }
+        const float fo0 = r == 0 ? P::ld(d.fsrc, 0, i, N) : 0.0f;
+        // density and the velocity of the last collision (own populations)
+        float drx = fo0, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            drx += foa[k] + fob[k];
+            const float df = foa[k] - fob[k];
+            j0 += (float)TRIO_EX(k) * df;
+            j1 += (float)TRIO_EY(k) * df;
+            j2 += (float)TRIO_EZ(k) * df;
+        }
+        drx = trio_sum(drx, b3);
+        j0 = trio_sum(j0, b3);
+        j1 = trio_sum(j1, b3);
+        j2 = trio_sum(j2, b3);
+        const float rx = 1.0f + drx;
+        const float irx = __frcp_rn(rx);
+        const float ux = j0 * irx - ax, uy = j1 * irx - ay, uz = j2 * irx - az;
+        // the arriving populations: pull, Eq. noslip from an obstacle or a
+        // wall, gas sources reconstructed below; the mass exchange of the link
+        // back to a liquid or interface source; the fill level seen there
+        float fpa[3], fpb[3], dm = 0.0f, fsa = phx, fsb = phx;
+        unsigned solid = 0, gas = 0, seen_lg = 0;  // per direction slot 2k (a), 2k + 1 (b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int q = s ? TRIO_QB(k) : TRIO_QA(k);
+                const int si = s ? sb[k] : sa[k];
+                const int ns = si < 0 ? CL_WALL : (s ? cb[k] : ca[k]);
+                const float pq = s ? pb[k] : pa[k];
+                const float phy = (float)(s ? hb[k] : ha[k]);
+                const float fbar = s ? foa[k] : fob[k];  // own population of the opposite direction
+                const unsigned bit = 1u << (2 * k + s);
+                float fv = pq, seen = phx;
+                seen_lg |= ns == CL_L ? 1u : (ns == CL_G ? 2u : 0u);
+                if (ns == CL_WALL || ns == CL_O) {
+                    solid |= bit;
+                    const float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
+                                                 : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
+                    fv = fbar + 6.0f * (k == 0 ? wf(1) : wf(7)) * cuw * rx;
+                } else if (ns == CL_G) {
+                    gas |= bit;
+                    fv = 0.0f;
+                    seen = 0.0f;
+                } else if (ns == CL_L) {
+                    dm += pq - fbar;
+                    seen = 1.0f;
+                } else {
+                    dm += 0.5f * (phx + phy) * (pq - fbar);
+                    seen = phy;
+                }
+                if (s) fpb[k] = fv;
+                else fpa[k] = fv;
+                if (k == 0) {
+                    if (s) fsb = seen;
+                    else fsa = seen;
+                }
+            }
+        }
+        // normal n = -grad(phi): component r from the member's axis pair
+        // (W/E pull from x + e_x / x - e_x, N/S from x - e_y / x + e_y, T/B
+        // from x - e_z / x + e_z)
+        const float nvr = r == 0 ? 0.5f * (fsb - fsa) : 0.5f * (fsa - fsb);
+        const float nv0 = __shfl_sync(FULL, nvr, b3), nv1 = __shfl_sync(FULL, nvr, b3 + 1),
+                    nv2 = __shfl_sync(FULL, nvr, b3 + 2);
+        float drg = d.drg_f;
+        if (d.sigma != 0.0) {
+            // gas density raised by the Laplace pressure (curvature by member 0)
+            const float len = sqrtf((nv0 * nv0 + nv1 * nv1) + nv2 * nv2);
+            const float nu0 = len > 0.0f ? nv0 / len : 0.0f, nu1 = len > 0.0f ? nv1 / len : 0.0f,
+                        nu2 = len > 0.0f ? nv2 / len : 0.0f;
+            float kap = 0.0f;
+            if (r == 0) kap = curvature_f(d, x, y, z, nu0, nu1, nu2);
+            kap = __shfl_sync(FULL, kap, b3);
+            drg = d.drg_f + (6.0f * d.sigma_f) * kap;
+        }
+        // Eq. reconstruct for gas-sourced directions and every non-solid
+        // direction with c.n below the dead band
+        const float usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float cn = (float)TRIO_EX(k) * nv0 + (float)TRIO_EY(k) * nv1 + (float)TRIO_EZ(k) * nv2;  // c_a . n
+            const float cu = (float)TRIO_EX(k) * ux + (float)TRIO_EY(k) * uy + (float)TRIO_EZ(k) * uz;
+            const float w = k == 0 ? wf(1) : wf(7);
+            const float fe = feq_dev_cu(w, cu, usq, drg) + feq_dev_cu(w, -cu, usq, drg);
+            const unsigned ba = 1u << (2 * k), bb = 2u << (2 * k);
+            if ((gas & ba) || (cn < -d.deadband_f && !(solid & ba))) fpa[k] = fe - fob[k];
+            if ((gas & bb) || (-cn < -d.deadband_f && !(solid & bb))) fpb[k] = fe - foa[k];
+        }
+        dm = trio_sum(dm, b3);
+        // BGK + Luo force on the deviations (the pair split of collide_store_v)
+        const float fp0 = r == 0 ? fo0 : 0.0f;
+        float dr = fp0, k0 = 0.0f, k1 = 0.0f, k2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dr += fpa[k] + fpb[k];
+            const float df = fpa[k] - fpb[k];
+            k0 += (float)TRIO_EX(k) * df;
+            k1 += (float)TRIO_EY(k) * df;
+            k2 += (float)TRIO_EZ(k) * df;
+        }
+        dr = trio_sum(dr, b3);
+        k0 = trio_sum(k0, b3);
+        k1 = trio_sum(k1, b3);
+        k2 = trio_sum(k2, b3);
+        const float rho = 1.0f + dr;
+        const float inv = __frcp_rn(rho);
+        const float vx = k0 * inv, vy = k1 * inv, vz = k2 * inv;
+        const float nusq15 = (vx * vx + vy * vy + vz * vz) * -1.5f;
+        const float nua3 = (vx * ax + vy * ay + vz * az) * -3.0f;
+        const float om = d.omega_f, om1 = 1.0f - om;
+        void *gdst = d.fdst;
+        float rest = 0.0f, drs = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float w = k == 0 ? wf(1) : wf(7);
+            const float wdr = dr * w, wr = rho * w, wr3 = wr * 3.0f;
+            // p = the member with the positive leading component, m the other
+            const float sgk = TRIO_POS(k) ? 1.0f : -1.0f;
+            const float cpx = sgk * (float)TRIO_EX(k), cpy = sgk * (float)TRIO_EY(k), cpz = sgk * (float)TRIO_EZ(k);
+            const float cu = cpx * vx + cpy * vy + cpz * vz;
+            const float ca = cpx * ax + cpy * ay + cpz * az;
+            const float A = fmaf(wr, fmaf(cu * cu, 4.5f, nusq15), wdr);
+            const float C = wr * fmaf(cu, 9.0f * ca, nua3);
+            const float E = fmaf(A, om, C);
+            const float G = fmaf(wr3 * cu, om, wr3 * ca);
+            const bool a_is_p = TRIO_POS(k) != 0;
+            const float fp_p = a_is_p ? fpa[k] : fpb[k], fp_m = a_is_p ? fpb[k] : fpa[k];
+            const float dnp = fmaf(fp_p, om1, E + G), dnm = fmaf(fp_m, om1, E - G);
+            const int qp = a_is_p ? TRIO_QA(k) : TRIO_QB(k), qm = a_is_p ? TRIO_QB(k) : TRIO_QA(k);
+            float stp = dnp, stm = dnm;
+            if (valid) {
+                stp = trio_st<S>(gdst, qp, i32, N, dnp);
+                stm = trio_st<S>(gdst, qm, i32, N, dnm);
+            }
+            rest += (fp_p - stp) + (fp_m - stm);
+            drs += stp + stm;
+        }
+        rest = trio_sum(rest, b3);
+        if (r == 0) {
+            const float st0 = fp0 + rest;
+            if (valid) P::st_one(gdst, 0, i, N, st0);
+            drs += st0;
+        }
+        drs = trio_sum(drs, b3);
+        const unsigned lg = __shfl_sync(FULL, seen_lg, b3) | __shfl_sync(FULL, seen_lg, b3 + 1) |
+                            __shfl_sync(FULL, seen_lg, b3 + 2);
+        const bool has_l = lg & 1u, has_g = lg & 2u;
+        uint8_t mk = 0;
+        if (valid && r == 0) {
+            const double m_new = d.m[i] + (double)dm;
+            const double phin = m_new / (1.0 + (double)drs);
+            d.m[i] = m_new;
+            d.phidst[i] = phin;
+            if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
+            mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+            // an interface cell without a liquid neighbour empties, one without
+            // a gas neighbour fills
+            if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
+            if (mk) d.cmark[i] = mk;
+        }
+        wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
+        wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
+    }
+}
+#undef TRIO_QA
+#undef TRIO_QB
+#undef TRIO_EX
+#undef TRIO_EY
+#undef TRIO_EZ
+#undef TRIO_POS
+
+// ---- C1 + C2 for interface cells (Sec. 2.2): reconstruction, mass exchange.
+// Double storage: one thread per cell, every sum in the order of the oracle.
+__device__ __forceinline__ void interface_d(const Dev &d, const VB &vb) {
+    using P = Sto<0>;
     const long long N = d.N;
     // the bulk kernel has read this step's fluid top: clear the slot for the
     // next step to record into
@@ -1941,206 +2330,110 @@ __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
         int x, y, z;
         coords(d, i, x, y, z);
         double own_phi = d.phisrc[i];
-        double m_new;
-        if constexpr (!P::shifted) {
-            long long src[Q];
-            int scl[Q];
-            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
+        long long src[Q];
+        int scl[Q];
+        bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                scl[q] = cls(d, src[q]);
-                has_l = has_l || scl[q] == CL_L;
-                has_g = has_g || scl[q] == CL_G;
-            }
-            // normal n = -grad(phi), central differences
-            double nv[3];
-            {
-                double pm = fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi);
-                double pp = fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi);
-                nv[0] = 0.5 * (pm - pp);
-                pm = fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi);
-                pp = fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi);
-                nv[1] = 0.5 * (pm - pp);
-                pm = fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi);
-                pp = fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi);
-                nv[2] = 0.5 * (pm - pp);
-            }
-            double fo[Q], fp[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
-            double rho_x = 0.0;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) rho_x += fo[q];
-            double j0 = 0.0, j1 = 0.0, j2 = 0.0;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                j0 += cx(q) * fo[q];
-                j1 += cy(q) * fo[q];
-                j2 += cz(q) * fo[q];
-            }
-            double ux[3] = {j0 / rho_x - d.a[0], j1 / rho_x - d.a[1], j2 / rho_x - d.a[2]};
-            // gas density of the boundary condition, raised by the Laplace pressure
-            double rg = d.rho_g;
-            if (d.sigma != 0.0) {
-                double nc[3];
-                unit_vec_d(nv, nc);
-                rg = d.rho_g + (6.0 * d.sigma) * curvature_d(d, x, y, z, nc[0], nc[1], nc[2]);
-            }
-            fp[0] = fo[0];
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                int qb = opp(q);
-                if (scl[q] == CL_WALL || scl[q] == CL_O) {
-                    double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q)
-                                                : (d.walls_move ? wall_cuw(d, x, y, z, q) : 0.0);
-                    fp[q] = fo[qb] + ((6.0 * wd(q)) * rho_x) * cuw;
-                } else if (scl[q] == CL_G) {
-                    fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
-                } else {
-                    fp[q] = P::ld(d.fsrc, q, src[q], N);
-                }
-            }
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
-                if (cn < -d.deadband && scl[q] != CL_O && scl[q] != CL_WALL) {
-                    int qb = opp(q);
-                    fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
-                }
-            }
-            double dm = 0.0;
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                int qb = opp(q);
-                long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
-                int yc = cls(d, yi);
-                if (yc == CL_L) {
-                    dm += P::ld(d.fsrc, qb, yi, N) - fo[q];
-                } else if (yc == CL_I) {
-                    double wgt = 0.5 * (own_phi + d.phisrc[yi]);
-                    dm += wgt * (P::ld(d.fsrc, qb, yi, N) - fo[q]);
-                }
-            }
-            m_new = d.m[i] + dm;
-            double fn[Q];
-            collide_d(d, fp, fn);
-            double r = 0.0;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                P::st(d.fdst, q, i, N, fn[q]);
-                r += fn[q];
-            }
-            double phin = m_new / r;
-            d.m[i] = m_new;
-            d.phidst[i] = phin;
-            if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
-            uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
-            // an interface cell without a liquid neighbour empties, one without
-            // a gas neighbour fills
-            if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
-            if (mk) d.cmark[i] = mk;
-            wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
-            wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
-        } else {
-            float phx = (float)own_phi;
-            float fo[Q], fp[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
-            float drx = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                drx += fo[q];
-                if (cx(q)) j0 += cx(q) * fo[q];
-                if (cy(q)) j1 += cy(q) * fo[q];
-                if (cz(q)) j2 += cz(q) * fo[q];
-            }
-            float rx = 1.0f + drx;
-            float ux = j0 / rx - d.a_f[0], uy = j1 / rx - d.a_f[1], uz = j2 / rx - d.a_f[2];
-            // One walk over the 18 neighbours s = x - c_q: the class decides the
-            // arriving population (pull, or Eq. noslip from an obstacle or a
-            // wall; gas sources are reconstructed below); a liquid or interface
-            // source also gives the Sec. 2.2 mass exchange of the link back to
-            // it, f_q(s) - f_qbar(x) (weighted by the mean fill for interface
-            // neighbours), and the axis neighbours give the fill levels of the
-            // normal (1 / phi / 0 for liquid / interface / gas, own phi else).
-            fp[0] = fo[0];
-            unsigned solid = 0, gas = 0;  // directions whose source is solid / gas
-            bool has_l = false, has_g = false;  // any liquid / gas among the 18 neighbours
-            float dm = 0.0f;
-            float fs[7];  // fill level seen at the source of each axis direction
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const int qb = opp(q);
-                const long long si = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
-                const int ns = cls(d, si);
-                has_l = has_l || ns == CL_L;
-                has_g = has_g || ns == CL_G;
-                float seen = phx;
-                if (ns == CL_WALL || ns == CL_O) {
-                    solid |= 1u << q;
-                    float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
-                                           : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
-                    fp[q] = fo[qb] + 6.0f * wf(q) * cuw * rx;
-                } else if (ns == CL_G) {
-                    gas |= 1u << q;
-                    fp[q] = 0.0f;
-                    seen = 0.0f;
-                } else {
-                    const float pq = P::ld(d.fsrc, q, si, N);
-                    fp[q] = pq;
-                    if (ns == CL_L) {
-                        dm += pq - fo[qb];
-                        seen = 1.0f;
-                    } else {
-                        const float phy = (float)d.phisrc[si];
-                        dm += 0.5f * (phx + phy) * (pq - fo[qb]);
-                        seen = phy;
-                    }
-                }
-                if (q <= 6) fs[q] = seen;
-            }
-            // normal n = -grad(phi): W, E, N, S, T, B pull from x + e_x, x - e_x,
-            // x - e_y, x + e_y, x - e_z, x + e_z
-            const float nv0 = 0.5f * (fs[2] - fs[1]), nv1 = 0.5f * (fs[3] - fs[4]), nv2 = 0.5f * (fs[5] - fs[6]);
-            float drg = d.drg_f;
-            if (d.sigma != 0.0) {
-                // gas density raised by the Laplace pressure
-                const float len = sqrtf((nv0 * nv0 + nv1 * nv1) + nv2 * nv2);
-                const float nu0 = len > 0.0f ? nv0 / len : 0.0f, nu1 = len > 0.0f ? nv1 / len : 0.0f,
-                            nu2 = len > 0.0f ? nv2 / len : 0.0f;
-                drg = d.drg_f + (6.0f * d.sigma_f) * curvature_f(d, x, y, z, nu0, nu1, nu2);
-            }
-            // Eq. reconstruct for gas-sourced directions and every non-solid
-            // direction with c.n below the dead band
-#pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const float cn = cx(q) * nv0 + cy(q) * nv1 + cz(q) * nv2;
-                if ((gas & (1u << q)) || (cn < -d.deadband_f && !(solid & (1u << q)))) {
-                    const int qb = opp(q);
-                    fp[q] = feq_dev_f(q, drg, ux, uy, uz) + feq_dev_f(qb, drg, ux, uy, uz) - fo[qb];
-                }
-            }
-            m_new = d.m[i] + (double)dm;
-            void *g = d.fdst;
-            float drs = 0.0f;
-            float rho = collide_store_v<1, float>(d, fp, [&](int q, float v) {
-                float st = P::st_one(g, q, i, N, v);
-                drs += st;
-                return st;
-            });
-            double r = 1.0 + (double)drs;
-            double phin = m_new / r;
-            d.m[i] = m_new;
-            d.phidst[i] = phin;
-            if (!(rho > 0.0f) || !(rho < 1e30f)) atomicOr(d.status, ST_NONFINITE);
-            uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
-            if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
-            if (mk) d.cmark[i] = mk;
-            wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
-            wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
+        for (int q = 1; q < Q; ++q) {
+            src[q] = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q));
+            scl[q] = cls(d, src[q]);
+            has_l = has_l || scl[q] == CL_L;
+            has_g = has_g || scl[q] == CL_G;
         }
+        // normal n = -grad(phi), central differences
+        double nv[3];
+        {
+            double pm = fill_seen(d, nbr(d, x, y, z, -1, 0, 0), own_phi);
+            double pp = fill_seen(d, nbr(d, x, y, z, 1, 0, 0), own_phi);
+            nv[0] = 0.5 * (pm - pp);
+            pm = fill_seen(d, nbr(d, x, y, z, 0, -1, 0), own_phi);
+            pp = fill_seen(d, nbr(d, x, y, z, 0, 1, 0), own_phi);
+            nv[1] = 0.5 * (pm - pp);
+            pm = fill_seen(d, nbr(d, x, y, z, 0, 0, -1), own_phi);
+            pp = fill_seen(d, nbr(d, x, y, z, 0, 0, 1), own_phi);
+            nv[2] = 0.5 * (pm - pp);
+        }
+        double fo[Q], fp[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) fo[q] = P::ld(d.fsrc, q, i, N);
+        double rho_x = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) rho_x += fo[q];
+        double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            j0 += cx(q) * fo[q];
+            j1 += cy(q) * fo[q];
+            j2 += cz(q) * fo[q];
+        }
+        double ux[3] = {j0 / rho_x - d.a[0], j1 / rho_x - d.a[1], j2 / rho_x - d.a[2]};
+        // gas density of the boundary condition, raised by the Laplace pressure
+        double rg = d.rho_g;
+        if (d.sigma != 0.0) {
+            double nc[3];
+            unit_vec_d(nv, nc);
+            rg = d.rho_g + (6.0 * d.sigma) * curvature_d(d, x, y, z, nc[0], nc[1], nc[2]);
+        }
+        fp[0] = fo[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            int qb = opp(q);
+            if (scl[q] == CL_WALL || scl[q] == CL_O) {
+                double cuw = scl[q] == CL_O ? link_cuw(d, d.bodies[d.bid[src[q]]], x, y, z, q)
+                                            : (d.walls_move ? wall_cuw(d, x, y, z, q) : 0.0);
+                fp[q] = fo[qb] + ((6.0 * wd(q)) * rho_x) * cuw;
+            } else if (scl[q] == CL_G) {
+                fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
+            } else {
+                fp[q] = P::ld(d.fsrc, q, src[q], N);
+            }
+        }
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            double cn = (cx(q) * nv[0] + cy(q) * nv[1]) + cz(q) * nv[2];
+            if (cn < -d.deadband && scl[q] != CL_O && scl[q] != CL_WALL) {
+                int qb = opp(q);
+                fp[q] = (feq_d(q, rg, ux) + feq_d(qb, rg, ux)) - fo[qb];
+            }
+        }
+        double dm = 0.0;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            int qb = opp(q);
+            long long yi = nbr(d, x, y, z, cx(q), cy(q), cz(q));
+            int yc = cls(d, yi);
+            if (yc == CL_L) {
+                dm += P::ld(d.fsrc, qb, yi, N) - fo[q];
+            } else if (yc == CL_I) {
+                double wgt = 0.5 * (own_phi + d.phisrc[yi]);
+                dm += wgt * (P::ld(d.fsrc, qb, yi, N) - fo[q]);
+            }
+        }
+        const double m_new = d.m[i] + dm;
+        double fn[Q];
+        collide_d(d, fp, fn);
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            P::st(d.fdst, q, i, N, fn[q]);
+            r += fn[q];
+        }
+        double phin = m_new / r;
+        d.m[i] = m_new;
+        d.phidst[i] = phin;
+        if (!(r == r) || r <= 0.0) atomicOr(d.status, ST_NONFINITE);
+        uint8_t mk = phin >= 1.0 + d.eps ? MK_FILLED : (phin <= -d.eps ? MK_EMPTIED : 0);
+        // an interface cell without a liquid neighbour empties, one without
+        // a gas neighbour fills
+        if (!mk && d.nb_rule) mk = (!has_l && has_g) ? MK_EMPTIED : ((!has_g && has_l) ? MK_FILLED : 0);
+        if (mk) d.cmark[i] = mk;
+        wl_append(d, mk == MK_FILLED, WL_FILLED, (uint32_t)i);
+        wl_append(d, mk == MK_EMPTIED, WL_EMPTIED, (uint32_t)i);
     }
+}
+template <int S> __device__ __forceinline__ void interface_body(const Dev &d, const VB &vb) {
+    if constexpr (S == 0) interface_d(d, vb);
+    else interface_trio<S>(d, vb);
 }
 template <int S>
 __global__ void __launch_bounds__(128, LBMFS_IFACE_MINB) k_interface(const __grid_constant__ Dev d) {
@@ -2836,6 +3129,7 @@ template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MIN
 template <int S, int ZB>
 LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB),
                  (bulk_body<S, ZB>(d, vb, zb)))
+template <int S> LBMFS_BATCH_BODY(BkGeneral, GEN_THREADS, 1, general_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
@@ -2917,6 +3211,8 @@ template <int S> struct Launch {
             }
         }
         mark();
+        k_general<S><<<LIST_BLOCKS, GEN_THREADS, 0, st>>>(d);
+        mark();
         k_interface<S><<<LBMFS_IFACE_GRID, 128, 0, st>>>(d);
         mark();
         k_conv_filled<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
@@ -2943,7 +3239,7 @@ template <int S> struct Launch {
         mark();
         if (d.nb > 0) k_nb_update<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(d);
         mark();
-        return d.nb > 0 ? 15 : 9;  // kernels (the counter reset is a memset node)
+        return d.nb > 0 ? 16 : 10;  // kernels (the counter reset is a memset node)
     }
 };
 
@@ -2961,6 +3257,8 @@ template <int S> struct BatchStep {
         batch_launch<BkForces<S>>(b, SH_FORCE, dim3(32, 8), st);
         mark();
         batch_bulk_launch<S>(b, st);
+        mark();
+        batch_launch<BkGeneral<S>>(b, SH_IFACE, GEN_THREADS, st);
         mark();
         batch_launch<BkInterface<S>>(b, SH_IFACE, 128, st);
         mark();
@@ -2989,8 +3287,8 @@ template <int S> struct BatchStep {
         batch_launch<BkNbUpdate>(b, SH_LIST, LIST_THREADS, st);
         mark();
         int n = 0;
-        const int shapes[] = {SH_TANK, SH_FORCE, SH_BULK, SH_IFACE, SH_LIST, SH_LIST, SH_LIST, SH_LIST, SH_LIST,
-                              SH_LIST, SH_LIST, SH_BODY, SH_FORCE, SH_FORCE, SH_ONE, SH_LIST};
+        const int shapes[] = {SH_TANK, SH_FORCE, SH_BULK, SH_IFACE, SH_IFACE, SH_LIST, SH_LIST, SH_LIST, SH_LIST,
+                              SH_LIST, SH_LIST, SH_LIST, SH_BODY, SH_FORCE, SH_FORCE, SH_ONE, SH_LIST};
         for (int sh : shapes) n += b.sh[sh].n ? 1 : 0;
         return n;
     }
@@ -3004,7 +3302,7 @@ template <int S> struct BatchStep {
 };
 
 inline const char *const *kernel_names() {
-    static const char *const n[] = {"reset_counters", "forces", "liquid", "interface", "conv_filled",
+    static const char *const n[] = {"reset_counters", "forces", "liquid", "general", "interface", "conv_filled",
                                     "conv_emptied",    "conv_init", "conv_flags", "conv_claim", "conv_excess",
                                     "conv_finish",     "bodies",  "remap_cover", "remap_pending", "remap_resolve", "nb_update"};
     return n;
@@ -3021,7 +3319,7 @@ template <int S> KernelSet make_kernel_set() {
     k.batch_step = &BatchStep<S>::step;
     k.batch_bulk = &BatchStep<S>::bulk;
     k.bulk_blocks_per_sm = &BatchStep<S>::bulk_blocks_per_sm;
-    k.nkernels = 16;
+    k.nkernels = 17;
     k.names = kernel_names();
     return k;
 }

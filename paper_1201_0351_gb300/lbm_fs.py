@@ -64,7 +64,7 @@ class lbm_fs_stats_t(C.Structure):
                 ("uncovered", C.c_double), ("lost_excess", C.c_double), ("n_interface", C.c_int64),
                 ("n_filled", C.c_int64), ("n_emptied", C.c_int64), ("n_new_from_gas", C.c_int64),
                 ("n_new_from_liquid", C.c_int64), ("n_pending", C.c_int64), ("status", C.c_uint32),
-                ("kernel_launches", C.c_int64), ("wall_source", C.c_double)]
+                ("kernel_launches", C.c_int64), ("wall_source", C.c_double), ("n_general", C.c_int64)]
 
 
 class lbm_fs_batch_config_t(C.Structure):
