@@ -2144,6 +2144,7 @@ __device__ __forceinline__ void interface_trio(const Dev &d, const VB &vb) {
             hb[k] = __ldg(d.phisrc + lb);
         }
         const float fo0 = r == 0 ? P::ld(d.fsrc, 0, i, N) : 0.0f;
+        const double m_old = r == 0 ? d.m[i] : 0.0;  // requested with the populations
         // density and the velocity of the last collision (own populations)
         float drx = fo0, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
 #pragma unroll
@@ -2177,24 +2178,20 @@ __device__ __forceinline__ void interface_trio(const Dev &d, const VB &vb) {
                 const float phy = (float)(s ? hb[k] : ha[k]);
                 const float fbar = s ? foa[k] : fob[k];  // own population of the opposite direction
                 const unsigned bit = 1u << (2 * k + s);
-                float fv = pq, seen = phx;
-                seen_lg |= ns == CL_L ? 1u : (ns == CL_G ? 2u : 0u);
-                if (ns == CL_WALL || ns == CL_O) {
-                    solid |= bit;
-                    const float cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q)
-                                                 : (d.walls_move ? (float)wall_cuw(d, x, y, z, q) : 0.0f);
-                    fv = fbar + 6.0f * (k == 0 ? wf(1) : wf(7)) * cuw * rx;
-                } else if (ns == CL_G) {
-                    gas |= bit;
-                    fv = 0.0f;
-                    seen = 0.0f;
-                } else if (ns == CL_L) {
-                    dm += pq - fbar;
-                    seen = 1.0f;
-                } else {
-                    dm += 0.5f * (phx + phy) * (pq - fbar);
-                    seen = phy;
-                }
+                const bool sol = ns == CL_WALL || ns == CL_O, gs = ns == CL_G, lq = ns == CL_L;
+                // selects rather than branches: the lanes of a warp meet every
+                // class, and branches would run one after another; only the
+                // moving-solid term (rare) is behind a branch
+                float cuw = 0.0f;
+                if (ns == CL_O || (sol && d.walls_move))
+                    cuw = ns == CL_O ? link_cuw_f(d, d.bodies[d.bid[si]], x, y, z, q) : (float)wall_cuw(d, x, y, z, q);
+                seen_lg |= lq ? 1u : (gs ? 2u : 0u);
+                solid |= sol ? bit : 0u;
+                gas |= gs ? bit : 0u;
+                const float fv = sol ? fbar + 6.0f * (k == 0 ? wf(1) : wf(7)) * cuw * rx : (gs ? 0.0f : pq);
+                const float wgt = lq ? 1.0f : 0.5f * (phx + phy);
+                dm += (sol || gs) ? 0.0f : wgt * (pq - fbar);
+                const float seen = sol ? phx : (gs ? 0.0f : (lq ? 1.0f : phy));
                 if (s) fpb[k] = fv;
                 else fpa[k] = fv;
                 if (k == 0) {
@@ -2294,7 +2291,7 @@ __device__ __forceinline__ void interface_trio(const Dev &d, const VB &vb) {
         const bool has_l = lg & 1u, has_g = lg & 2u;
         uint8_t mk = 0;
         if (valid && r == 0) {
-            const double m_new = d.m[i] + (double)dm;
+            const double m_new = m_old + (double)dm;
             const double phin = m_new / (1.0 + (double)drs);
             d.m[i] = m_new;
             d.phidst[i] = phin;
