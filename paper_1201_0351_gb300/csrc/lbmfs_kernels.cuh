@@ -889,8 +889,8 @@ __device__ __forceinline__ VB vb_own() { return VB{blockIdx.x, blockIdx.y, block
          it_##var += vb.nx * blockDim.x)
 
 // neighbour-obstacle bit: set when any of the 18 neighbours is an obstacle
-// (the bulk kernel then takes its general path; walls and periodic seams are
-// recognised from the cell's coordinates)
+// (the bulk kernel then lists the cell for k_general; walls and periodic
+// seams are recognised from the cell's coordinates)
 __device__ __forceinline__ void nb_refresh(const Dev &d, long long i) {
     int x, y, z;
     coords(d, i, x, y, z);
