@@ -54,6 +54,10 @@ struct Body {
     int mode, shape;  // shape 0: box of half extents h; 1: sphere of radius h[0]
     int lo[3], hi[3];   // cells that may be inside at the current pose, [lo, hi)
     int plo[3], phi[3]; // the same at the previous pose
+    // the pose in float for the inside pre-test: centre split into its
+    // integer part oi and fraction of, R and the half extents rounded to float
+    int oi[3];
+    float of[3], Rf[9], hf[3];
 };
 
 // Everything a kernel needs, passed by value.
