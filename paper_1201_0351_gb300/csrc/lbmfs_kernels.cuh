@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ constexpr float wf(int q) {
 #define LBMFS_FORCE_MINB 3  // resident 256-thread blocks per SM of the float-storage force kernel
 #endif
 #ifndef LBMFS_FORCE_ROWS
-#define LBMFS_FORCE_ROWS 1  // range rows per warp in the float-storage force kernel
+#define LBMFS_FORCE_ROWS 1  // 32-cell tasks of a body's range per warp in the float-storage force kernel
 #endif
 #ifndef LBMFS_IFACE_MINB
 #define LBMFS_IFACE_MINB 6  // resident blocks per SM asked of ptxas for the interface kernel (80 registers)
@@ -1203,19 +1203,26 @@ __device__ __forceinline__ void forces_float_body(const Dev &d, const VB &vb) {
     const int lx = hi[0] - lo[0];
     const unsigned ly = (unsigned)(hi[1] - lo[1]), nrows = ly * (unsigned)(hi[2] - lo[2]);
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    // as many of the body's blocks as give each warp LBMFS_FORCE_ROWS rows;
-    // the others contribute zeros
+    // the range's cells in x-fastest order, 32 consecutive cells per warp
+    // task (a row shorter or longer than 32 cells leaves no lanes idle); as
+    // many of the body's blocks as give each warp LBMFS_FORCE_ROWS tasks, the
+    // others contribute zeros
+    const unsigned ncell = (unsigned)lx * nrows, ntask = (ncell + 31u) / 32u;
     const unsigned per_block = (unsigned)nwarp * LBMFS_FORCE_ROWS;
-    const unsigned used = min((unsigned)vb.nx, (nrows + per_block - 1) / per_block);
+    const unsigned used = min((unsigned)vb.nx, (ntask + per_block - 1) / per_block);
     if ((unsigned)vb.x >= used) {
         if (tid < 7) d.part[((long long)bi * FORCE_BLOCKS + vb.x) * 7 + tid] = 0.0;
         return;
     }
-    for (unsigned row = (unsigned)vb.x * nwarp + wid; row < nrows; row += used * nwarp) {
-        int y = lo[1] + (int)(row % ly), z = lo[2] + (int)(row / ly);
-        if (y < 0 || y >= d.ny) y = ((y % d.ny) + d.ny) % d.ny;  // only periodic axes leave [0, n)
-        if (z < 0 || z >= d.nz) z = ((z % d.nz) + d.nz) % d.nz;
-        for (int xo = lane; xo < lx; xo += 32) {
+    for (unsigned task = (unsigned)vb.x * nwarp + wid; task < ntask; task += used * nwarp) {
+        {
+            const unsigned kc = task * 32u + (unsigned)lane;
+            if (kc >= ncell) continue;
+            const unsigned row = kc / (unsigned)lx;
+            const int xo = (int)(kc - row * (unsigned)lx);
+            int y = lo[1] + (int)(row % ly), z = lo[2] + (int)(row / ly);
+            if (y < 0 || y >= d.ny) y = ((y % d.ny) + d.ny) % d.ny;  // only periodic axes leave [0, n)
+            if (z < 0 || z >= d.nz) z = ((z % d.nz) + d.nz) % d.nz;
             int x = lo[0] + xo;
             if (x < 0 || x >= d.nx) x = ((x % d.nx) + d.nx) % d.nx;
             const long long i = x + sy * (y + (long long)d.ny * z);
