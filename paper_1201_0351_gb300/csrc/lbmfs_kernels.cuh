@@ -2753,7 +2753,8 @@ __global__ void k_conv_finish(const __grid_constant__ Dev d) { conv_finish_body<
 
 // ----------------------------------------------- C5: rigid-body update
 // (the role the paper gives the pe engine, Sec. 2.3: the body moves under the
-// hydrodynamic force and torque and gravity; the integrator is this build's)
+// hydrodynamic force and torque and gravity; the paper does not give the
+// integrator, this one is a virtual-mass explicit update)
 
 // one warp per body: fixed-order sum of the force partials, then the update
 __device__ __forceinline__ void body_step(const Dev &d, Body &b, const double *acc);
