@@ -3172,7 +3172,9 @@ template <int S> LBMFS_BATCH_BODY_SM(BkForces, 256, S == 0 ? 2 : LBMFS_FORCE_MIN
 template <int S, int ZB>
 LBMFS_BATCH_BODY(BkLiquid, BULK_THREADS, S == 0 ? 1 : (LBMFS_BULK_PAIR ? LBMFS_PAIR_MINB : LBMFS_BULK_MINB),
                  (bulk_body<S, ZB>(d, vb, zb)))
-template <int S> LBMFS_BATCH_BODY(BkGeneral, GEN_THREADS, 1, general_body<S>(d, vb))
+// the batch's listed cells are spread over many more blocks: 4 resident per SM
+// (128 registers) beat 1 there, not on the single tank
+template <int S> LBMFS_BATCH_BODY(BkGeneral, GEN_THREADS, 4, general_body<S>(d, vb))
 template <int S> LBMFS_BATCH_BODY(BkInterface, 128, LBMFS_IFACE_MINB, interface_body<S>(d, vb))
 LBMFS_BATCH_BODY(BkConvFilled, LIST_THREADS, 1, conv_filled_body(d, vb))
 LBMFS_BATCH_BODY(BkConvEmptied, LIST_THREADS, 1, conv_emptied_body(d, vb))
